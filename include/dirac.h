@@ -1,0 +1,181 @@
+/*
+ * dirac.h -- C ABI of the GB300 Dirac Lanczos propagator.
+ *
+ * The library advances a two-component spinor field on a uniform 2D grid by
+ * the Lanczos (Krylov) approximation of the time-evolution operator of the
+ * discretised Dirac equation (Beerwerth & Bauke, "Krylov subspace methods for
+ * the Dirac equation"):
+ *
+ *   H = c sigma.(p - qA) + sigma_z m c^2 + V          (Sec. 3, Eq. 12; q = -1)
+ *   psi(t+dt) = exp(-i H dt) psi ~ ||psi|| Q exp(-i T dt) e_1   (Sec. 4, Eq. 17)
+ *
+ * with Q, T from the Lanczos recurrence (Sec. 2, Fig. 1 with the modified
+ * Gram-Schmidt alpha of Eq. 4) and the error estimate of Eq. 18.
+ *
+ * Conventions shared by every call:
+ *  - a spinor field is complex128 laid out [ny][nx][2] (x fastest, then the
+ *    upper and lower component of one site adjacent): 32 bytes per site,
+ *    row-major, no padding.  Device pointers must be 32-byte aligned.
+ *  - site (j, l) sits at x = (j - nx/2) dx, y = (l - ny/2) dy (atomic units).
+ *  - all work is enqueued on the context's CUDA stream and is asynchronous
+ *    unless a call says it synchronises.
+ *  - no call aborts or throws; each returns a dirac_status.  Device-side
+ *    failures (non-finite values) are recorded on the device and returned by
+ *    the next call that synchronises (an info request, dirac_sync).
+ *  - the caller owns every buffer it passes; the library owns the context
+ *    and its workspace (the Krylov basis lives in device memory).
+ */
+#ifndef DIRAC_GB300_H
+#define DIRAC_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DIRAC_OK = 0,
+    DIRAC_EINVAL = 1,      /* an argument is out of range (see dirac_last_error) */
+    DIRAC_ENOMEM = 2,      /* device or pinned host allocation failed */
+    DIRAC_ECUDA = 3,       /* a CUDA runtime call failed */
+    DIRAC_ENONFINITE = 4,  /* NaN/Inf met in a reduction; psi left unchanged */
+    DIRAC_ESTATE = 5       /* call out of order (e.g. step before set_fields) */
+} dirac_status;
+
+enum { DIRAC_PERIODIC = 0, DIRAC_DIRICHLET = 1 };
+enum { DIRAC_FP64 = 0 };
+
+/* Largest Krylov dimension m one step may use. */
+#define DIRAC_KRYLOV_MAX 32
+
+typedef struct dirac_ctx dirac_ctx;
+
+/* Diagnostics of the most recent step (Sec. 4 and Sec. 6). */
+typedef struct {
+    int k_used;        /* Krylov dimension used (< m after breakdown or tol) */
+    int breakdown;     /* 1 if the recurrence stopped on beta_k ~ 0 */
+    double err_est;    /* Eq. 18: dt beta_k ||psi|| |e_k^T exp(-i T dt) e_1| */
+    double cum_err;    /* sum of err_est since create (Sec. 6, cumulative bound) */
+    double norm;       /* ||psi|| before the step (sum over sites, no dx dy) */
+    double energy;     /* <psi|H|psi>/<psi|psi> before the step (hartree) */
+    double alpha[DIRAC_KRYLOV_MAX];  /* T diagonal, of H - energy_shift (hartree) */
+    double beta[DIRAC_KRYLOV_MAX];   /* beta[i] couples i, i+1; beta[k-1] = beta_k */
+} dirac_step_info;
+
+/*
+ * Create a propagator for an nx-by-ny grid with spacings dx, dy (bohr),
+ * particle mass and speed of light c (atomic units), central finite
+ * differences of stencil_order 2 or 4 (Sec. 7: finite differences; the
+ * central form keeps H Hermitian), DIRAC_PERIODIC or DIRAC_DIRICHLET
+ * boundaries, precision DIRAC_FP64, and Krylov dimension up to m_max
+ * (1..DIRAC_KRYLOV_MAX).  Allocates the workspace: (m_max + 1) device fields
+ * of nx*ny sites.  cuda_stream is a cudaStream_t (NULL: the legacy default
+ * stream).  On success *out owns the context.
+ * Errors: DIRAC_EINVAL (nx, ny < 1; dx, dy, c <= 0; mass < 0; bad order,
+ * boundary, precision or m_max), DIRAC_ENOMEM, DIRAC_ECUDA.
+ */
+dirac_status dirac_create(dirac_ctx** out, int nx, int ny, double dx, double dy,
+                          double mass, double c, int stencil_order, int boundary,
+                          int precision, int m_max, void* cuda_stream);
+
+/* Free the context and its workspace (synchronises its stream). NULL is a no-op. */
+void dirac_destroy(dirac_ctx* ctx);
+
+/* Change the stream later work is enqueued on. */
+dirac_status dirac_set_stream(dirac_ctx* ctx, void* cuda_stream);
+
+/*
+ * Set the fields of Eq. 12 for the following steps.  V_dev: device float64
+ * [ny][nx] potential energy q*phi in hartree (copied into the context, the
+ * caller keeps its buffer), or NULL for V = 0.  A_x, A_y: the spatially
+ * uniform vector potential for the next step -- for a time-dependent field
+ * the caller passes the mean of A over the step (the first Magnus term,
+ * Eq. 16; dirac_pulse_sin2_mean computes it for a sin^2 pulse).
+ * energy_shift s: the recurrence runs on H - s and the step multiplies by
+ * exp(-i s dt) -- exact in exact arithmetic; reported alpha are of H - s.
+ * Errors: DIRAC_EINVAL (non-finite scalars), DIRAC_ECUDA.
+ */
+dirac_status dirac_set_fields(dirac_ctx* ctx, const double* V_dev, double A_x, double A_y,
+                              double energy_shift);
+
+/* Update only the uniform vector potential (cheap; keeps V and the shift). */
+dirac_status dirac_set_vector_potential(dirac_ctx* ctx, double A_x, double A_y);
+
+/*
+ * One time step, in place: psi_dev <- exp(-i H dt) psi_dev by Eq. 17 with a
+ * Krylov space of dimension m (1..m_max).  tol > 0 stops the recurrence at the
+ * first k whose Eq. 18 estimate is <= tol * ||psi||; tol = 0 always uses m
+ * (unless the recurrence breaks down, beta_k <= 1e-12 times the largest
+ * |alpha_j + s| or beta_j so far).  psi_dev: device complex128 [ny][nx][2],
+ * 32-byte aligned, owned by the caller.  If info is non-NULL the call
+ * synchronises the stream and fills it; otherwise it returns after enqueueing.
+ * Errors: DIRAC_EINVAL (m out of range, dt <= 0 or non-finite, tol < 0,
+ * misaligned psi, dt too large for the small exponential: dt * ||H|| > 90),
+ * DIRAC_ESTATE (no set_fields yet), DIRAC_ENONFINITE (only with info),
+ * DIRAC_ECUDA.
+ */
+dirac_status dirac_lanczos_step(dirac_ctx* ctx, void* psi_dev, double dt, int m, double tol,
+                                dirac_step_info* info);
+
+/*
+ * nsteps steps in place, the vector potential of step n being
+ * (A_xy_host[2n], A_xy_host[2n+1]) (host array of 2*nsteps doubles), or the
+ * current one for every step if A_xy_host is NULL.  info (optional) describes
+ * the last step and synchronises.  Errors as dirac_lanczos_step.
+ */
+dirac_status dirac_lanczos_steps(dirac_ctx* ctx, void* psi_dev, int nsteps, double dt, int m,
+                                 double tol, const double* A_xy_host, dirac_step_info* info);
+
+/*
+ * As dirac_lanczos_steps, but psi_host is a HOST complex128 [ny][nx][2]
+ * buffer: the call copies it to a device buffer owned by the context, runs
+ * the steps, copies the result back and synchronises.  Pinned host memory
+ * makes the copies asynchronous DMA; pageable memory also works.
+ */
+dirac_status dirac_propagate_host(dirac_ctx* ctx, void* psi_host, int nsteps, double dt, int m,
+                                  double tol, const double* A_xy_host, dirac_step_info* info);
+
+/* Wait for the context's stream; returns a pending device error if any. */
+dirac_status dirac_sync(dirac_ctx* ctx);
+
+/* Mean of A_x(t) = a0 sin^2(pi t/T) sin(omega t) (zero outside [0, T]) over
+ * [t0, t0 + dt], in closed form: the first Magnus term of Eq. 16. */
+double dirac_pulse_sin2_mean(double t0, double dt, double a0, double omega, double duration);
+
+/* Number of kernels the library launched on this context so far. */
+long long dirac_kernel_launches(const dirac_ctx* ctx);
+
+/*
+ * Per-kernel device timing with CUDA events, for tracing and benchmarks.
+ * While enabled, the context records an event on its stream before every
+ * kernel it launches and after every time step.  dirac_profile_read waits
+ * for the last recorded event and returns, per kernel kind, the device time
+ * (ms) between each kernel's event and the next one, and the number of
+ * launches, accumulated since the previous read; it then clears the record.
+ * Kinds: 0 = Lanczos pass (stencil + reductions), 1 = recombination.
+ * ms and launches point to DIRAC_KERNEL_KINDS elements each.
+ */
+#define DIRAC_KERNEL_KINDS 2
+dirac_status dirac_profile_enable(dirac_ctx* ctx, int enable);
+dirac_status dirac_profile_read(dirac_ctx* ctx, double* ms, long long* launches);
+
+/* Static description of a status code. */
+const char* dirac_status_string(dirac_status s);
+
+/* Message of the last error raised on the calling thread ("" if none). */
+const char* dirac_last_error(void);
+
+/*
+ * Test hook for the device small-matrix exponential: v = exp(-i T dt) e_1 for
+ * the k-by-k tridiagonal T (alpha[0..k-1] diagonal, beta[0..k-2] off
+ * diagonal), whose spectrum must lie in [lo, hi], computed by the same device
+ * routine the propagator uses.  Host arrays in and out (v_re, v_im: k each);
+ * synchronises.  Errors: DIRAC_EINVAL (k out of 1..DIRAC_KRYLOV_MAX, lo > hi,
+ * dt * (hi - lo) / 2 > 90), DIRAC_ECUDA.
+ */
+dirac_status dirac_debug_tridiag_expm(const double* alpha, const double* beta, int k, double dt,
+                                      double lo, double hi, double* v_re, double* v_im);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DIRAC_GB300_H */

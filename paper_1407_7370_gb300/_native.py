@@ -1,0 +1,90 @@
+"""ctypes binding of include/dirac.h (argument marshalling only).
+
+Every computation happens in the CUDA library; if the library is missing or
+cannot be loaded this module raises -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+from . import build as _build
+
+_lib = None
+
+HEADER = os.path.join(_build.ROOT, "include", "dirac.h")
+KRYLOV_MAX = 32
+KERNEL_KINDS = 2
+
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ESTATE = range(6)
+PERIODIC, DIRICHLET = 0, 1
+FP64 = 0
+
+
+class StepInfoC(ctypes.Structure):
+    _fields_ = [("k_used", ctypes.c_int), ("breakdown", ctypes.c_int),
+                ("err_est", ctypes.c_double), ("cum_err", ctypes.c_double),
+                ("norm", ctypes.c_double), ("energy", ctypes.c_double),
+                ("alpha", ctypes.c_double * KRYLOV_MAX), ("beta", ctypes.c_double * KRYLOV_MAX)]
+
+
+class DiracError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("dirac status %d (%s): %s" % (status, status_string(status), message))
+        self.status = status
+
+
+def header_functions() -> list:
+    """Names of the functions declared in include/dirac.h."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return re.findall(r"\b(dirac_[a-z_0-9]+)\s*\(", text)
+
+
+def lib():
+    """Load the built library (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError("CUDA library %s not built; run paper_1407_7370_gb300.build.build()"
+                           % _build.LIB)
+    L = ctypes.CDLL(_build.LIB)
+    vp, i, d, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "dirac_create": (i, [ctypes.POINTER(vp), i, i, d, d, d, d, i, i, i, i, vp]),
+        "dirac_destroy": (None, [vp]),
+        "dirac_set_stream": (i, [vp, vp]),
+        "dirac_set_fields": (i, [vp, vp, d, d, d]),
+        "dirac_set_vector_potential": (i, [vp, d, d]),
+        "dirac_lanczos_step": (i, [vp, vp, d, i, d, ctypes.POINTER(StepInfoC)]),
+        "dirac_lanczos_steps": (i, [vp, vp, i, d, i, d, dp, ctypes.POINTER(StepInfoC)]),
+        "dirac_propagate_host": (i, [vp, vp, i, d, i, d, dp, ctypes.POINTER(StepInfoC)]),
+        "dirac_sync": (i, [vp]),
+        "dirac_pulse_sin2_mean": (d, [d, d, d, d, d]),
+        "dirac_kernel_launches": (ctypes.c_longlong, [vp]),
+        "dirac_status_string": (ctypes.c_char_p, [i]),
+        "dirac_last_error": (ctypes.c_char_p, []),
+        "dirac_debug_tridiag_expm": (i, [dp, dp, i, d, d, d, dp, dp]),
+        "dirac_profile_enable": (i, [vp, i]),
+        "dirac_profile_read": (i, [vp, dp, ctypes.POINTER(ctypes.c_longlong)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def status_string(s: int) -> str:
+    try:
+        return lib().dirac_status_string(s).decode()
+    except Exception:  # pragma: no cover - only used in error paths
+        return "?"
+
+
+def check(status: int) -> None:
+    if status != OK:
+        raise DiracError(status, lib().dirac_last_error().decode())

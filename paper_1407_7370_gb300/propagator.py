@@ -1,0 +1,175 @@
+"""Python front end of the C ABI: a thin object over dirac_create/.../dirac_destroy."""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+
+import numpy as np
+
+from . import _native as nat
+
+
+@dataclasses.dataclass
+class StepInfo:
+    k_used: int
+    breakdown: bool
+    err_est: float
+    cum_err: float
+    norm: float
+    energy: float
+    alpha: np.ndarray
+    beta: np.ndarray
+
+
+def _info(c: nat.StepInfoC) -> StepInfo:
+    k = c.k_used
+    return StepInfo(k, bool(c.breakdown), c.err_est, c.cum_err, c.norm, c.energy,
+                    np.array(c.alpha[:k]), np.array(c.beta[:k]))
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr():
+    torch = _torch()
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _check_psi(psi, ny, nx):
+    torch = _torch()
+    if not isinstance(psi, torch.Tensor) or not psi.is_cuda:
+        raise TypeError("psi must be a CUDA torch tensor")
+    if psi.dtype != torch.complex128 or tuple(psi.shape) != (ny, nx, 2) or not psi.is_contiguous():
+        raise ValueError("psi must be contiguous complex128 of shape (%d, %d, 2)" % (ny, nx))
+
+
+class Propagator:
+    """Lanczos propagator for one grid; see include/dirac.h for the semantics."""
+
+    def __init__(self, nx: int, ny: int, dx: float, dy: float, mass: float = 1.0,
+                 c: float = 137.036, order: int = 2, boundary: str = "periodic", m_max: int = 20):
+        L = nat.lib()
+        self.nx, self.ny = nx, ny
+        b = {"periodic": nat.PERIODIC, "dirichlet": nat.DIRICHLET}[boundary]
+        self._ctx = ctypes.c_void_p()
+        self._stream = _stream_ptr()
+        nat.check(L.dirac_create(ctypes.byref(self._ctx), nx, ny, dx, dy, mass, c, order, b,
+                                 nat.FP64, m_max, self._stream))
+
+    def _sync_stream(self):
+        s = _stream_ptr()
+        if s.value != self._stream.value:
+            nat.check(nat.lib().dirac_set_stream(self._ctx, s))
+            self._stream = s
+
+    def set_fields(self, V=None, A=(0.0, 0.0), shift: float = 0.0):
+        """V: CUDA float64 tensor (ny, nx) of potential energy, or None."""
+        self._sync_stream()
+        ptr = None
+        if V is not None:
+            torch = _torch()
+            if V.dtype != torch.float64 or not V.is_cuda or tuple(V.shape) != (self.ny, self.nx) \
+                    or not V.is_contiguous():
+                raise ValueError("V must be a contiguous CUDA float64 tensor (ny, nx)")
+            ptr = ctypes.c_void_p(V.data_ptr())
+        nat.check(nat.lib().dirac_set_fields(self._ctx, ptr, float(A[0]), float(A[1]), float(shift)))
+
+    def set_vector_potential(self, ax: float, ay: float = 0.0):
+        nat.check(nat.lib().dirac_set_vector_potential(self._ctx, float(ax), float(ay)))
+
+    def step(self, psi, dt: float, m: int, tol: float = 0.0, info: bool = False):
+        return self.steps(psi, 1, dt, m, tol, None, info)
+
+    def steps(self, psi, nsteps: int, dt: float, m: int, tol: float = 0.0, A=None,
+              info: bool = False):
+        """nsteps in place; A: optional (nsteps, 2) array of per-step vector potentials."""
+        _check_psi(psi, self.ny, self.nx)
+        self._sync_stream()
+        a_ptr, a_arr = None, None
+        if A is not None:
+            a_arr = np.ascontiguousarray(A, dtype=np.float64).reshape(nsteps, 2)
+            a_ptr = a_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        out = nat.StepInfoC() if info else None
+        nat.check(nat.lib().dirac_lanczos_steps(self._ctx, ctypes.c_void_p(psi.data_ptr()), nsteps,
+                                                dt, m, tol, a_ptr,
+                                                ctypes.byref(out) if info else None))
+        return _info(out) if info else None
+
+    def propagate_host(self, psi_host, nsteps: int, dt: float, m: int, tol: float = 0.0, A=None):
+        """psi_host: host complex128 (ny, nx, 2) buffer (numpy array or pinned CPU tensor),
+        updated in place; host<->device copies happen inside the call."""
+        if isinstance(psi_host, np.ndarray):
+            if psi_host.dtype != np.complex128 or psi_host.shape != (self.ny, self.nx, 2) \
+                    or not psi_host.flags.c_contiguous:
+                raise ValueError("psi_host must be C-contiguous complex128 (ny, nx, 2)")
+            ptr = psi_host.ctypes.data
+        else:
+            torch = _torch()
+            if psi_host.is_cuda or psi_host.dtype != torch.complex128 or not psi_host.is_contiguous():
+                raise ValueError("psi_host must be a contiguous CPU complex128 tensor")
+            ptr = psi_host.data_ptr()
+        self._sync_stream()
+        a_ptr, a_arr = None, None
+        if A is not None:
+            a_arr = np.ascontiguousarray(A, dtype=np.float64).reshape(nsteps, 2)
+            a_ptr = a_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        out = nat.StepInfoC()
+        nat.check(nat.lib().dirac_propagate_host(self._ctx, ctypes.c_void_p(ptr), nsteps, dt, m,
+                                                 tol, a_ptr, ctypes.byref(out)))
+        return _info(out)
+
+    def sync(self):
+        nat.check(nat.lib().dirac_sync(self._ctx))
+
+    def profile(self, enable: bool = True):
+        """Start/stop per-kernel CUDA-event timing (see dirac_profile_enable)."""
+        nat.check(nat.lib().dirac_profile_enable(self._ctx, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        """{kind: (total ms, launches)} since the previous read; kinds 'pass', 'recombine'."""
+        ms = (ctypes.c_double * nat.KERNEL_KINDS)()
+        n = (ctypes.c_longlong * nat.KERNEL_KINDS)()
+        nat.check(nat.lib().dirac_profile_read(self._ctx, ms, n))
+        return {"pass": (ms[0], n[0]), "recombine": (ms[1], n[1])}
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(nat.lib().dirac_kernel_launches(self._ctx))
+
+    def close(self):
+        if getattr(self, "_ctx", None) is not None and self._ctx.value:
+            nat.lib().dirac_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pulse_sin2_mean(t0: float, dt: float, a0: float, omega: float, duration: float) -> float:
+    """Magnus-1 mean of A0 sin^2(pi t/T) sin(omega t) over [t0, t0+dt] (library, closed form)."""
+    return float(nat.lib().dirac_pulse_sin2_mean(t0, dt, a0, omega, duration))
+
+
+def pulse_schedule(t0: float, dt: float, nsteps: int, a0: float, omega: float, duration: float):
+    """(nsteps, 2) per-step vector potentials (A_x mean, 0) for a sin^2 pulse."""
+    out = np.zeros((nsteps, 2))
+    for n in range(nsteps):
+        out[n, 0] = pulse_sin2_mean(t0 + n * dt, dt, a0, omega, duration)
+    return out
+
+
+def tridiag_expm_device(alpha, beta, dt: float, lo: float, hi: float) -> np.ndarray:
+    """exp(-i T dt) e_1 by the device routine (test hook)."""
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    k = a.size
+    b = np.ascontiguousarray(np.concatenate([np.asarray(beta, dtype=np.float64), [0.0]])[: max(k, 1)])
+    vr, vi = np.zeros(k), np.zeros(k)
+    P = ctypes.POINTER(ctypes.c_double)
+    nat.check(nat.lib().dirac_debug_tridiag_expm(a.ctypes.data_as(P), b.ctypes.data_as(P), k, dt,
+                                                 lo, hi, vr.ctypes.data_as(P), vi.ctypes.data_as(P)))
+    return vr + 1j * vi

@@ -1,0 +1,256 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU FP64 oracle.
+
+Tolerance (FP64 path): relative L2 of psi at most 1e-10 per unit of simulated
+time, the propagation target of this library, with a floor of 1e-14 per step
+for runs too short for that to exceed rounding (both sides round differently:
+the GPU sums in a different order and evaluates exp(-iT dt) e_1 by a
+Chebyshev expansion where the oracle diagonalises T).
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import free
+from oracle import hamiltonian as ham
+from oracle import lanczos as lz
+from paper_1407_7370_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+C = 137.036
+
+
+def fp64_tol(steps, dt):
+    return max(1e-10 * steps * dt, 1e-14 * steps)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1407_7370_gb300 import build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+
+
+def gpu_run(grid, psi0, dt, m, steps, V=None, A=(0.0, 0.0), order=2, boundary="periodic",
+            shift=0.0, tol=0.0, A_steps=None, info=True):
+    from paper_1407_7370_gb300 import Propagator
+    prop = Propagator(grid.nx, grid.ny, grid.dx, grid.dy, order=order, boundary=boundary, m_max=m)
+    prop.set_fields(None if V is None else torch.from_numpy(V).cuda(), A=A, shift=shift)
+    psi = torch.from_numpy(np.ascontiguousarray(psi0)).cuda()
+    inf = prop.steps(psi, steps, dt, m, tol=tol, A=A_steps, info=info)
+    return psi.cpu().numpy(), inf, prop
+
+
+def oracle_op(grid, V=None, A=(0.0, 0.0), order=2, boundary=ham.PERIODIC, shift=0.0):
+    return ham.Operator(grid.nx, grid.ny, grid.dx, grid.dy, order=order, boundary=boundary,
+                        V=V, A=A, shift=shift)
+
+
+# ---------------------------------------------------------------------------
+def test_device_small_exponential_matches_scipy():
+    import scipy.linalg
+    from paper_1407_7370_gb300 import tridiag_expm_device
+    rng = np.random.default_rng(0)
+    for k in (1, 2, 5, 10, 20, 32):
+        for R in (0.05, 2.0, 10.0, 40.0):
+            alpha = rng.uniform(-1, 1, k)
+            beta = np.abs(rng.uniform(0.1, 0.5, max(k - 1, 0)))
+            T = np.diag(alpha) + np.diag(beta, 1) + np.diag(beta, -1)
+            ev = np.linalg.eigvalsh(T)
+            lo, hi = ev[0] - 0.1, ev[-1] + 0.1
+            dt = R / (0.5 * (hi - lo))
+            ref = scipy.linalg.expm(-1j * dt * T)[:, 0]
+            v = tridiag_expm_device(alpha, beta, dt, lo, hi)
+            assert np.max(np.abs(v - ref)) <= 2e-14 * (1 + R), (k, R)
+
+
+def test_free_packet_64_full_run_matches_oracle():
+    """64x64, dx=0.1, m=10, dt=1e-4, 100 steps: the oracle-sized propagation case."""
+    cfg = wl.FREE_PACKET_64
+    g = cfg["grid"]
+    psi0 = wl.positive_energy_packet(g, p0=cfg["p0"], sigma_x=cfg["sigma_x"])
+    out, info, _ = gpu_run(g, psi0, cfg["dt"], cfg["m"], cfg["steps"])
+    ref, infos = lz.propagate(oracle_op(g), psi0.copy(), cfg["dt"], cfg["m"], cfg["steps"])
+    err = lz.rel_l2(out, ref)
+    assert err <= 1e-10 * cfg["steps"] * cfg["dt"], err
+    # both against the closed-form free propagation, within the cumulative bound (Sec. 6)
+    exact = free.propagate(oracle_op(g), psi0.copy(), cfg["dt"], cfg["steps"])
+    cum = sum(i.err_est for i in infos)
+    assert ham.norm(out - exact) <= cum + 1e-12 * ham.norm(exact)
+    # estimates below ~1e-14 ||psi|| are rounding noise on both sides
+    assert abs(info.cum_err - cum) <= 1e-6 * cum + 1e-14 * ham.norm(psi0) * cfg["steps"]
+
+
+def test_step_scalars_match_oracle():
+    g = wl.Grid(64, 48, 0.1, 0.1)
+    psi0 = wl.positive_energy_packet(g, p0=(10.0, 5.0))
+    V = wl.smoothed_coulomb(g, 3.0, 0.5)
+    dt, m = 1e-4, 12
+    out, info, _ = gpu_run(g, psi0, dt, m, 1, V=V, A=(4.0, -2.0))
+    ref, oi = lz.krylov_step(oracle_op(g, V=V, A=(4.0, -2.0)), psi0.copy(), dt, m)
+    assert info.k_used == oi.k_used == m
+    assert np.allclose(info.alpha, oi.alpha / dt, rtol=1e-12, atol=1e-10)
+    assert np.allclose(info.beta[: m - 1], oi.beta[: m - 1] / dt, rtol=1e-9, atol=1e-9)
+    assert abs(info.beta[m - 1] - oi.beta[m - 1] / dt) <= 1e-6 * oi.beta[m - 1] / dt
+    assert abs(info.err_est - oi.err_est) <= 1e-6 * oi.err_est + 1e-14 * oi.norm
+    assert abs(info.energy - oi.energy) <= 1e-12 * abs(oi.energy)
+    assert abs(info.norm - oi.norm) <= 1e-13 * oi.norm
+    assert lz.rel_l2(out, ref) <= fp64_tol(1, dt)
+
+
+def test_error_estimate_matches_oracle_when_it_is_large():
+    g = wl.Grid(64, 64, 0.1, 0.1)
+    psi0 = wl.positive_energy_packet(g, p0=(10.0, 0.0)) + 0.05 * wl.random_spinor(g, 3)
+    for m in (2, 3, 4):
+        out, info, _ = gpu_run(g, psi0, 1e-4, m, 1)
+        ref, oi = lz.krylov_step(oracle_op(g), psi0.copy(), 1e-4, m)
+        assert oi.err_est > 1e-10 * oi.norm
+        assert abs(info.err_est - oi.err_est) <= 1e-6 * oi.err_est
+        assert lz.rel_l2(out, ref) <= 1e-12
+
+
+CASES = [
+    # nx, ny, order, boundary, V, A
+    (37, 23, 2, "periodic", True, (3.0, -1.5)),
+    (33, 9, 4, "periodic", True, (0.0, 2.0)),
+    (40, 17, 2, "dirichlet", True, (1.0, 1.0)),
+    (35, 11, 4, "dirichlet", False, (2.5, 0.0)),
+    (3, 5, 2, "periodic", True, (1.0, 0.5)),
+    (7, 1, 2, "periodic", False, (1.0, 0.0)),
+    (1, 9, 4, "dirichlet", True, (0.0, 0.3)),
+    (64, 8, 2, "periodic", False, (0.0, 0.0)),
+]
+
+
+@pytest.mark.parametrize("nx,ny,order,boundary,hasv,A", CASES)
+def test_ragged_small_and_boundary_grids(nx, ny, order, boundary, hasv, A):
+    g = wl.Grid(nx, ny, 0.1, 0.13)
+    psi0 = wl.random_spinor(g, nx * 100 + ny) * 0.1
+    V = wl.random_potential(g, 7, scale=20.0) if hasv else None
+    dt, m, steps = 1e-4, 6, 3
+    b = ham.DIRICHLET if boundary == "dirichlet" else ham.PERIODIC
+    out, info, _ = gpu_run(g, psi0, dt, m, steps, V=V, A=A, order=order, boundary=boundary)
+    ref, oinf = lz.propagate(oracle_op(g, V=V, A=A, order=order, boundary=b), psi0.copy(), dt, m, steps)
+    assert info.k_used == oinf[-1].k_used
+    assert lz.rel_l2(out, ref) <= fp64_tol(steps, dt)
+
+
+def test_tolerance_mode_matches_oracle_k():
+    g = wl.Grid(48, 48, 0.1, 0.1)
+    psi0 = wl.positive_energy_packet(g, p0=(10.0, 0.0))
+    dt, m = 1e-4, 20
+    for tol in (1e-7, 1e-10):
+        out, info, _ = gpu_run(g, psi0, dt, m, 1, tol=tol)
+        ref, oi = lz.krylov_step(oracle_op(g), psi0.copy(), dt, m, tol=tol)
+        assert info.k_used == oi.k_used < m
+        assert lz.rel_l2(out, ref) <= fp64_tol(1, dt)
+
+
+def test_breakdown_on_plane_wave_eigenvector():
+    from tests.test_oracle_hamiltonian import plane_wave_eigpair
+    g = wl.Grid(16, 16, 0.1, 0.1)
+    psi, E = plane_wave_eigpair(16, 16, 0.1, 0.1, 3, 1, 2, (2.0, 0.0), 0.0)
+    out, info, _ = gpu_run(g, psi, 1e-4, 10, 1, A=(2.0, 0.0))
+    assert info.k_used == 1 and info.breakdown
+    assert np.max(np.abs(out - np.exp(-1j * E * 1e-4) * psi)) <= 1e-13
+
+
+def test_energy_shift_does_not_change_the_step():
+    g = wl.Grid(32, 32, 0.1, 0.1)
+    psi0 = wl.positive_energy_packet(g, p0=(10.0, 0.0))
+    a, _, _ = gpu_run(g, psi0, 1e-4, 10, 5)
+    b, _, _ = gpu_run(g, psi0, 1e-4, 10, 5, shift=C * C)
+    assert lz.rel_l2(b, a) <= fp64_tol(5, 1e-4)
+
+
+def test_bitwise_deterministic():
+    g = wl.Grid(96, 80, 0.1, 0.1)
+    psi0 = wl.positive_energy_packet(g, p0=(10.0, 0.0))
+    V = wl.smoothed_coulomb(g, 2.0, 0.5)
+    a, ia, _ = gpu_run(g, psi0, 1e-4, 10, 4, V=V)
+    b, ib, _ = gpu_run(g, psi0, 1e-4, 10, 4, V=V)
+    assert np.array_equal(a, b) and ia.err_est == ib.err_est
+
+
+def test_nonfinite_input_is_reported_and_psi_kept():
+    from paper_1407_7370_gb300 import Propagator
+    from paper_1407_7370_gb300._native import DiracError, ENONFINITE
+    g = wl.Grid(32, 16, 0.1, 0.1)
+    psi0 = wl.positive_energy_packet(g)
+    psi0[3, 4, 1] = np.nan
+    prop = Propagator(32, 16, 0.1, 0.1, m_max=8)
+    prop.set_fields()
+    psi = torch.from_numpy(psi0.copy()).cuda()
+    with pytest.raises(DiracError) as e:
+        prop.step(psi, 1e-4, 8, info=True)
+    assert e.value.status == ENONFINITE
+    back = psi.cpu().numpy()
+    assert np.array_equal(np.isnan(back), np.isnan(psi0))
+    assert np.array_equal(np.nan_to_num(back), np.nan_to_num(psi0))
+    # the context stays usable
+    psi.copy_(torch.from_numpy(wl.positive_energy_packet(g)))
+    info = prop.step(psi, 1e-4, 8, info=True)
+    assert info.k_used == 8
+
+
+def test_invalid_arguments_are_rejected():
+    from paper_1407_7370_gb300 import Propagator
+    from paper_1407_7370_gb300 import _native as nat
+    g = wl.Grid(16, 16, 0.1, 0.1)
+    prop = Propagator(16, 16, 0.1, 0.1, m_max=8)
+    psi = torch.from_numpy(wl.positive_energy_packet(g)).cuda()
+    L = nat.lib()
+    p = ctypes.c_void_p(psi.data_ptr())
+    assert L.dirac_lanczos_step(prop._ctx, p, 1e-4, 8, 0.0, None) == nat.ESTATE
+    prop.set_fields()
+    assert L.dirac_lanczos_step(prop._ctx, p, 1e-4, 9, 0.0, None) == nat.EINVAL
+    assert L.dirac_lanczos_step(prop._ctx, p, 1e-4, 0, 0.0, None) == nat.EINVAL
+    assert L.dirac_lanczos_step(prop._ctx, p, 0.0, 8, 0.0, None) == nat.EINVAL
+    assert L.dirac_lanczos_step(prop._ctx, p, 1e-4, 8, -1.0, None) == nat.EINVAL
+    assert L.dirac_lanczos_step(prop._ctx, ctypes.c_void_p(psi.data_ptr() + 16), 1e-4, 8, 0.0,
+                                None) == nat.EINVAL
+    assert L.dirac_lanczos_step(prop._ctx, p, 1.0, 8, 0.0, None) == nat.EINVAL   # dt*||H|| > 90
+    assert L.dirac_sync(prop._ctx) == nat.OK
+
+
+def test_host_buffer_call_equals_device_call():
+    from paper_1407_7370_gb300 import Propagator
+    g = wl.Grid(64, 64, 0.1, 0.1)
+    psi0 = wl.positive_energy_packet(g, p0=(10.0, 0.0))
+    A = np.stack([np.linspace(0, 5, 6), np.zeros(6)], axis=1)
+    dev, _, _ = gpu_run(g, psi0, 1e-4, 10, 6, A_steps=A)
+    prop = Propagator(64, 64, 0.1, 0.1, m_max=10)
+    prop.set_fields()
+    host = torch.from_numpy(psi0.copy()).pin_memory()
+    prop.propagate_host(host, 6, 1e-4, 10, A=A)
+    assert np.array_equal(host.numpy(), dev)
+
+
+def test_kernel_launch_count():
+    g = wl.Grid(32, 32, 0.1, 0.1)
+    _, _, prop = gpu_run(g, wl.positive_energy_packet(g), 1e-4, 7, 3)
+    assert prop.kernel_launches == 1 + 3 * (7 + 1)   # probe + (m passes + recombine) per step
+
+
+@pytest.mark.slow
+def test_laser_packet_1024_full_size():
+    """1024x1024, dx=0.05, m=20, dt=2e-4 in the sin^2 laser pulse, as the benchmark runs it:
+    two steps element by element against the oracle, fifty against the closed form."""
+    from paper_1407_7370_gb300.propagator import pulse_schedule
+    cfg = wl.LASER_PACKET_1024
+    g, p = cfg["grid"], cfg["pulse"]
+    psi0 = wl.positive_energy_packet(g, p0=cfg["p0"], sigma_x=cfg["sigma_x"])
+    dt, m, t0 = cfg["dt"], cfg["m"], 0.3
+    A2 = pulse_schedule(t0, dt, 2, p.a0, p.omega, p.duration)
+    out, info, _ = gpu_run(g, psi0, dt, m, 2, A_steps=A2)
+    ref, oinf = lz.propagate(oracle_op(g), psi0.copy(), dt, m, 2, pulse=p, t0=t0)
+    assert lz.rel_l2(out, ref) <= fp64_tol(2, dt)
+    n = 50
+    An = pulse_schedule(t0, dt, n, p.a0, p.omega, p.duration)
+    out, info, _ = gpu_run(g, psi0, dt, m, n, A_steps=An)
+    exact = free.propagate(oracle_op(g), psi0.copy(), dt, n, pulse=p, t0=t0)
+    assert ham.norm(out - exact) <= info.cum_err + 1e-12 * ham.norm(exact)
+    assert abs(ham.norm(out) - ham.norm(psi0)) <= 1e-12 * ham.norm(psi0)

@@ -1,0 +1,72 @@
+"""CPU-side checks of the C ABI: the library builds, loads, exports every
+function that include/dirac.h declares, and its host-only pieces behave."""
+import ctypes
+
+import pytest
+
+from paper_1407_7370_gb300 import _native as nat
+from paper_1407_7370_gb300 import build as bld
+from paper_1407_7370_gb300 import workloads as wl
+
+
+@pytest.fixture(scope="session")
+def lib():
+    bld.build()
+    return nat.lib()
+
+
+def test_every_declared_function_is_exported(lib):
+    names = nat.header_functions()
+    assert len(names) >= 12
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings(lib):
+    for s in range(6):
+        assert lib.dirac_status_string(s)
+    assert lib.dirac_status_string(0) == b"ok"
+
+
+def test_pulse_mean_matches_oracle_quadrature(lib):
+    from oracle import fields
+    p = wl.SinSquaredPulse(50.0, 0.05, 1.0)
+    for t0 in (-3e-4, -1e-4, 0.0, 0.25, 0.77, 0.9999, 1.0, 1.5):
+        a = lib.dirac_pulse_sin2_mean(t0, 2e-4, p.a0, p.omega, p.duration)
+        b = fields.step_mean(p, t0, 2e-4)
+        assert abs(a - b) <= 1e-13 * p.a0
+
+
+def test_create_rejects_bad_arguments_before_touching_the_gpu(lib):
+    ctx = ctypes.c_void_p()
+    bad = [
+        (0, 8, 0.1, 0.1, 1.0, 137.0, 2, 0, 0, 10),
+        (8, 8, -0.1, 0.1, 1.0, 137.0, 2, 0, 0, 10),
+        (8, 8, 0.1, 0.1, 1.0, 0.0, 2, 0, 0, 10),
+        (8, 8, 0.1, 0.1, 1.0, 137.0, 3, 0, 0, 10),
+        (8, 8, 0.1, 0.1, 1.0, 137.0, 2, 5, 0, 10),
+        (8, 8, 0.1, 0.1, 1.0, 137.0, 2, 0, 7, 10),
+        (8, 8, 0.1, 0.1, 1.0, 137.0, 2, 0, 0, 0),
+        (8, 8, 0.1, 0.1, 1.0, 137.0, 2, 0, 0, 33),
+    ]
+    for args in bad:
+        assert lib.dirac_create(ctypes.byref(ctx), *args, None) == nat.EINVAL
+        assert lib.dirac_last_error()
+        assert not ctx.value
+
+
+def test_calls_on_null_context_fail_cleanly(lib):
+    assert lib.dirac_set_fields(None, None, 0.0, 0.0, 0.0) == nat.EINVAL
+    assert lib.dirac_lanczos_step(None, None, 1e-4, 10, 0.0, None) == nat.EINVAL
+    assert lib.dirac_sync(None) == nat.EINVAL
+    lib.dirac_destroy(None)
+
+
+def test_no_gpu_gives_cuda_error_not_a_crash(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    ctx = ctypes.c_void_p()
+    st = lib.dirac_create(ctypes.byref(ctx), 8, 8, 0.1, 0.1, 1.0, 137.036, 2, 0, 0, 4, None)
+    assert st in (nat.ECUDA, nat.ENOMEM)
+    assert not ctx.value
