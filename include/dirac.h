@@ -28,6 +28,8 @@
 #ifndef DIRAC_GB300_H
 #define DIRAC_GB300_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -163,6 +165,49 @@ const char* dirac_status_string(dirac_status s);
 
 /* Message of the last error raised on the calling thread ("" if none). */
 const char* dirac_last_error(void);
+
+/*
+ * Allocation-free single step.  The paper has no counterpart: this entry
+ * point exists for callers that must not allocate device memory -- a host
+ * framework that owns all device allocations and forbids libraries from
+ * calling cudaMalloc, a memory budget fixed up front, or a per-step loop in
+ * which an allocation's latency or failure is not acceptable.
+ *
+ * It performs one time step, in place on psi_dev, exactly as
+ * dirac_lanczos_step would for a context created with the same problem
+ * (dirac_problem below), but keeps its whole workspace in one static device
+ * array of dirac_noalloc_scratch_bytes() bytes (8 MiB) per device, and calls
+ * no cudaMalloc, cudaFree or other allocating routine.  Problems whose
+ * workspace, about (m + 1) * nx * ny * 32 bytes, does not fit are rejected
+ * with DIRAC_EINVAL.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call in the process shares the one array, and the array keeps the
+ *    previous call's contents (the call clears what must start at zero).
+ *    Calls whose work overlaps on the GPU -- on different streams, or from
+ *    different threads -- race on it: serialise them.
+ *  - With V_dev non-NULL the call reads two doubles back (the range of V)
+ *    and so synchronises the stream.  With info non-NULL it synchronises and
+ *    fills info (cum_err is this step's estimate); device-side errors
+ *    (DIRAC_ENONFINITE) are only reported when info is requested.
+ * psi_dev, V_dev: device buffers owned by the caller, laid out as for
+ * dirac_lanczos_step / dirac_set_fields.  cuda_stream: a cudaStream_t.
+ */
+typedef struct {
+    int nx, ny;
+    double dx, dy, mass, c;
+    int stencil_order, boundary;
+    const double* V_dev;          /* [ny][nx] potential energy or NULL */
+    double A_x, A_y, energy_shift;
+} dirac_problem;
+
+dirac_status dirac_lanczos_step_noalloc(const dirac_problem* problem, void* psi_dev, double dt,
+                                        int m, double tol, void* cuda_stream,
+                                        dirac_step_info* info);
+
+/* Size in bytes of the static scratch array used by dirac_lanczos_step_noalloc. */
+size_t dirac_noalloc_scratch_bytes(void);
 
 /*
  * Test hook for the device small-matrix exponential: v = exp(-i T dt) e_1 for

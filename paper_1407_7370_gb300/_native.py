@@ -29,6 +29,15 @@ class StepInfoC(ctypes.Structure):
                 ("alpha", ctypes.c_double * KRYLOV_MAX), ("beta", ctypes.c_double * KRYLOV_MAX)]
 
 
+class ProblemC(ctypes.Structure):
+    """dirac_problem of include/dirac.h (the allocation-free step's problem description)."""
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("dx", ctypes.c_double),
+                ("dy", ctypes.c_double), ("mass", ctypes.c_double), ("c", ctypes.c_double),
+                ("stencil_order", ctypes.c_int), ("boundary", ctypes.c_int),
+                ("V_dev", ctypes.c_void_p), ("A_x", ctypes.c_double), ("A_y", ctypes.c_double),
+                ("energy_shift", ctypes.c_double)]
+
+
 class DiracError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__("dirac status %d (%s): %s" % (status, status_string(status), message))
@@ -68,6 +77,9 @@ def lib():
         "dirac_last_error": (ctypes.c_char_p, []),
         "dirac_debug_tridiag_expm": (i, [dp, dp, i, d, d, d, dp, dp]),
         "dirac_profile_enable": (i, [vp, i]),
+        "dirac_lanczos_step_noalloc": (i, [ctypes.POINTER(ProblemC), vp, d, i, d, vp,
+                                           ctypes.POINTER(StepInfoC)]),
+        "dirac_noalloc_scratch_bytes": (ctypes.c_size_t, []),
         "dirac_profile_read": (i, [vp, dp, ctypes.POINTER(ctypes.c_longlong)]),
     }
     for name, (res, args) in sig.items():

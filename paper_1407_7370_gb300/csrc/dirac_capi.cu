@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -527,3 +528,217 @@ dirac_status dirac_debug_tridiag_expm(const double* alpha, const double* beta, i
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free single step (dirac_lanczos_step_noalloc).
+//
+// For callers that may not allocate device memory at all: a host framework
+// that owns every device allocation and forbids libraries from calling
+// cudaMalloc, a fixed memory budget decided up front, or a per-step loop in
+// which the latency or the failure of an allocation is not acceptable.  The
+// step keeps its whole workspace (scalar block, per-CTA partial sums, the two
+// y^ fields and the Krylov basis) in one file-scope device array of fixed
+// size, shared by every call in the process, and calls no cudaMalloc,
+// cudaFree or other allocating routine (host or device).
+// ===========================================================================
+namespace {
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = 8u << 20;   // 8 MiB per device
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::atomic<void*> g_noalloc_ptr[NOALLOC_MAX_DEVICES];
+
+// Device address of the scratch array on the current device.  In host code
+// `g_noalloc_scratch` names a host-side shadow, not device memory, so the
+// address is looked up once per device (with that device current).
+dirac_status noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(DIRAC_EINVAL, "device index %d too large", dev);
+  void* p = g_noalloc_ptr[dev].load();
+  if (!p) {
+    CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev].store(p);
+  }
+  *out = static_cast<unsigned char*>(p);
+  return DIRAC_OK;
+}
+
+size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Chebyshev coefficients as make_cheb, with stack storage only.
+dirac_status noalloc_cheb(double c0, double half, double dt, double shift, ChebParams& cp) {
+  const double R = half * dt;
+  if (!(R > 0.0) || R > 90.0)
+    return fail(DIRAC_EINVAL, "dt * ||H|| = %.3g outside (0, 90]: take smaller steps", R);
+  constexpr int NJ = 512;
+  double j[NJ + 2];
+  const int start = 2 * ((std::max(CHEB_MAX, (int)R) + 40 + (int)std::sqrt(40.0 * std::max(R, 1.0))) / 2);
+  if (start > NJ) return fail(DIRAC_EINVAL, "dt too large");
+  for (int k = 0; k <= start + 1; ++k) j[k] = 0.0;
+  j[start] = 1e-300;
+  for (int k = start; k >= 1; --k) {
+    j[k - 1] = (2.0 * k / R) * j[k] - j[k + 1];
+    if (std::fabs(j[k - 1]) > 1e250)
+      for (int t = k - 1; t <= start; ++t) j[t] *= 1e-250;
+  }
+  double norm = j[0];
+  for (int k = 2; k <= start; k += 2) norm += 2.0 * j[k];
+  int n = 2;
+  for (int k = 0; k < CHEB_MAX; ++k)
+    if (std::fabs(j[k] / norm) > 1e-18 || k <= (int)R + 1) n = k + 1;
+  if (n >= CHEB_MAX) return fail(DIRAC_EINVAL, "Chebyshev expansion needs more than %d terms", CHEB_MAX);
+  cp.n = std::max(n, 2);
+  cp.c0 = c0;
+  cp.inv_half = 1.0 / half;
+  const double ph = -(c0 + shift) * dt;
+  cp.ph_re = std::cos(ph);
+  cp.ph_im = std::sin(ph);
+  for (int k = 0; k < CHEB_MAX; ++k) {
+    const double a = (k == 0 ? 1.0 : 2.0) * (k < cp.n ? j[k] / norm : 0.0);
+    switch (k & 3) {
+      case 0: cp.cr[k] = a;  cp.ci[k] = 0.0; break;
+      case 1: cp.cr[k] = 0.0; cp.ci[k] = -a; break;
+      case 2: cp.cr[k] = -a; cp.ci[k] = 0.0; break;
+      default: cp.cr[k] = 0.0; cp.ci[k] = a; break;
+    }
+  }
+  return DIRAC_OK;
+}
+
+}  // namespace
+
+extern "C" size_t dirac_noalloc_scratch_bytes(void) { return NOALLOC_SCRATCH_BYTES; }
+
+extern "C" dirac_status dirac_lanczos_step_noalloc(const dirac_problem* pb, void* psi_dev, double dt,
+                                                   int m, double tol, void* cuda_stream,
+                                                   dirac_step_info* info) {
+  if (!pb || !psi_dev) return fail(DIRAC_EINVAL, "null argument");
+  const int nx = pb->nx, ny = pb->ny;
+  if (nx < 1 || ny < 1) return fail(DIRAC_EINVAL, "grid %d x %d must be at least 1 x 1", nx, ny);
+  if (!(pb->dx > 0) || !(pb->dy > 0) || !std::isfinite(pb->dx) || !std::isfinite(pb->dy))
+    return fail(DIRAC_EINVAL, "dx, dy must be finite and > 0");
+  if (!(pb->c > 0) || !std::isfinite(pb->c)) return fail(DIRAC_EINVAL, "c must be finite and > 0");
+  if (!(pb->mass >= 0) || !std::isfinite(pb->mass)) return fail(DIRAC_EINVAL, "mass must be finite and >= 0");
+  if (pb->stencil_order != 2 && pb->stencil_order != 4) return fail(DIRAC_EINVAL, "stencil_order must be 2 or 4");
+  if (pb->boundary != DIRAC_PERIODIC && pb->boundary != DIRAC_DIRICHLET) return fail(DIRAC_EINVAL, "bad boundary");
+  if (!std::isfinite(pb->A_x) || !std::isfinite(pb->A_y) || !std::isfinite(pb->energy_shift))
+    return fail(DIRAC_EINVAL, "non-finite field scalar");
+  if (m < 1 || m > DIRAC_KRYLOV_MAX) return fail(DIRAC_EINVAL, "m = %d outside 1..%d", m, DIRAC_KRYLOV_MAX);
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(DIRAC_EINVAL, "dt must be finite and > 0");
+  if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(DIRAC_EINVAL, "tol must be finite and >= 0");
+  if (!aligned32(psi_dev)) return fail(DIRAC_EINVAL, "psi must be 32-byte aligned");
+
+  // scratch layout: DevState | partials | y^[2] | basis[m-1]
+  const long long n = (long long)nx * ny;
+  const dim3 grid((nx + TX - 1) / TX, (ny + TY - 1) / TY);
+  const size_t ncta = (size_t)grid.x * grid.y;
+  const size_t field = round256((size_t)n * sizeof(vec4));
+  const size_t off_part = round256(sizeof(DevState));
+  const size_t off_y = off_part + round256(3 * sizeof(double) * ncta);
+  const size_t off_basis = off_y + 2 * field;
+  const size_t need = off_basis + (size_t)std::max(1, m - 1) * field;
+  if (need > NOALLOC_SCRATCH_BYTES)
+    return fail(DIRAC_EINVAL, "grid %d x %d with m = %d needs %zu bytes of scratch; the static scratch "
+                "holds %zu bytes (use dirac_create for larger problems)", nx, ny, m, need,
+                NOALLOC_SCRATCH_BYTES);
+  unsigned char* base = nullptr;
+  dirac_status s = noalloc_scratch(&base);
+  if (s != DIRAC_OK) return s;
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  DevState* st = reinterpret_cast<DevState*>(base);
+  double* partials = reinterpret_cast<double*>(base + off_part);
+  vec4* ybuf[2] = {reinterpret_cast<vec4*>(base + off_y), reinterpret_cast<vec4*>(base + off_y + field)};
+  vec4* basis = reinterpret_cast<vec4*>(base + off_basis);
+  vec4* psi = static_cast<vec4*>(psi_dev);
+
+  // the scratch keeps the previous call's contents: restart the scalar block
+  CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(DevState), stream));
+
+  // spectral interval of H - s (needs the range of V: read back two doubles)
+  double vmin = 0.0, vmax = 0.0;
+  if (pb->V_dev) {
+    double* mm = partials;   // two doubles of scratch, rewritten by the passes later
+    minmax_kernel<<<1, 256, 0, stream>>>(pb->V_dev, n, mm);
+    CUDA_TRY(cudaGetLastError());
+    double h[2];
+    CUDA_TRY(cudaMemcpyAsync(h, mm, sizeof(h), cudaMemcpyDeviceToHost, stream));
+    CUDA_TRY(cudaStreamSynchronize(stream));
+    if (!std::isfinite(h[0]) || !std::isfinite(h[1])) return fail(DIRAC_EINVAL, "V has non-finite entries");
+    vmin = h[0];
+    vmax = h[1];
+  }
+  double pf = 1.0;
+  if (pb->stencil_order == 4) {
+    const double cs = 1.0 - std::sqrt(6.0) / 2.0;
+    pf = std::sqrt(1.0 - cs * cs) * (4.0 - cs) / 3.0;
+  }
+  const double px = pf / pb->dx + std::fabs(pb->A_x), py = pf / pb->dy + std::fabs(pb->A_y);
+  const double mc2 = pb->mass * pb->c * pb->c;
+  const double emax = std::sqrt(mc2 * mc2 + pb->c * pb->c * (px * px + py * py));
+  const double c0 = 0.5 * (vmin + vmax) - pb->energy_shift;
+  const double half = (emax + 0.5 * (vmax - vmin)) * (1.0 + 1e-8) + 1e-12;
+
+  PassParams p;
+  std::memset(&p, 0, sizeof(p));
+  s = noalloc_cheb(c0, half, dt, pb->energy_shift, p.cheb);
+  if (s != DIRAC_OK) return s;
+  const double kfac = (pb->stencil_order == 2) ? 2.0 : 12.0;
+  p.psi = psi;
+  p.V = pb->V_dev;
+  p.st = st;
+  p.partials = partials;
+  p.nx = nx;
+  p.ny = ny;
+  p.m = m;
+  p.kx = pb->c / (kfac * pb->dx);
+  p.ky = pb->c / (kfac * pb->dy);
+  p.mcc = mc2;
+  p.cAx = pb->c * pb->A_x;
+  p.cAy = pb->c * pb->A_y;
+  p.shift = pb->energy_shift;
+  p.dt = dt;
+  p.tol = tol;
+
+  dirac_ctx view;   // launch configuration only; owns nothing
+  view.nx = nx; view.ny = ny; view.order = pb->stencil_order; view.boundary = pb->boundary;
+  view.has_v = pb->V_dev != nullptr; view.grid = grid; view.stream = stream;
+  p.pass = 1;
+  p.probe = 1;
+  CUDA_TRY(launch_pass(&view, p));
+  p.probe = 0;
+  for (int i = 1; i <= m; ++i) {
+    p.pass = i;
+    p.y_prev = (i >= 2) ? ybuf[(i - 1) & 1] : nullptr;
+    p.q_prev = (i == 2) ? psi : (i >= 3 ? basis + (size_t)(i - 3) * n : nullptr);
+    p.q_out = (i >= 2) ? basis + (size_t)(i - 2) * n : nullptr;
+    p.y_out = (i < m) ? ybuf[i & 1] : nullptr;
+    CUDA_TRY(launch_pass(&view, p));
+  }
+  int n_sm = 0, dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  const int rb = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, (long long)n_sm * 8));
+  recombine<<<rb, 256, 0, stream>>>(psi, basis, n, st);
+  CUDA_TRY(cudaGetLastError());
+
+  if (info) {
+    DevState h;
+    CUDA_TRY(cudaMemcpyAsync(&h, st, sizeof(DevState), cudaMemcpyDeviceToHost, stream));
+    CUDA_TRY(cudaStreamSynchronize(stream));
+    if (h.error) return fail(DIRAC_ENONFINITE, "non-finite value in a Lanczos reduction; psi left unchanged");
+    std::memset(info, 0, sizeof(*info));
+    info->k_used = h.k_used;
+    info->breakdown = h.breakdown;
+    info->err_est = h.err_est;
+    info->cum_err = h.err_est;
+    info->norm = h.psi_norm;
+    info->energy = h.energy;
+    for (int k = 0; k < h.k_used && k < DIRAC_KRYLOV_MAX; ++k) {
+      info->alpha[k] = h.alpha[k + 1];
+      info->beta[k] = h.beta[k + 1];
+    }
+  }
+  return DIRAC_OK;
+}
