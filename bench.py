@@ -33,12 +33,30 @@ if ROOT not in sys.path:
 
 from paper_1407_7370_gb300 import workloads as wl  # noqa: E402
 
-METRIC = "Lanczos H*psi site-updates/s (FP64 path)"
+METRIC = "Lanczos H*psi site-updates/s (FP64 path; mixed path in 'mixed')"
 UNIT = "site-updates/s"
 CFG = wl.LASER_PACKET_1024
 SITE_BYTES = 32            # complex128 spinor
 PASS_BYTES_PER_SITE = 3 * SITE_BYTES   # read q_i, read q_{i-1}, write q_{i+1} (V = 0)
+PASS_BYTES_PER_SITE_MIXED = 3 * 16      # the same accesses in complex64
 PASS_FLOPS_PER_SITE = 80   # FP64 flops of one Lanczos iteration per site
+
+# DRAM traffic per launch from the last ncu capture of the pass kernel, valid
+# only for the kernel source it was taken with (sha1 of dirac_kernels.cuh).
+TRAFFIC = {}
+
+
+def kernel_sha() -> str:
+    import hashlib
+    path = os.path.join(ROOT, "paper_1407_7370_gb300", "csrc", "dirac_kernels.cuh")
+    return hashlib.sha1(open(path, "rb").read()).hexdigest()[:12]
+
+
+def traffic_for(prec: str):
+    rec = TRAFFIC.get(prec)
+    if rec and rec[0] == kernel_sha():
+        return rec[1]
+    return None
 
 
 def parse():
@@ -48,6 +66,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", choices=["fp64", "mixed"], default=None,
+                    help="run one path only (for profiling); prints a partial line")
     return ap.parse_args()
 
 
@@ -170,6 +190,55 @@ def run_reference(args):
 # ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
+def measure(prop, psi, A, K, W, world, dist, torch, gi):
+    """Time K steps (CUDA events on the launch stream), then K profiled steps
+    (per-kernel event timing), then end-to-end steps through the host-buffer
+    call.  Returns a dict of raw numbers."""
+    g, m, dt = CFG["grid"], CFG["m"], CFG["dt"]
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(t):
+        if world > 1:
+            tt = torch.tensor([t], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t = float(tt.item())
+        return t
+
+    prop.steps(psi, W, dt, m, A=A[:W])
+    barrier()
+    clocks = ClockSampler(gi)
+    clocks.start()
+    l0 = prop.kernel_launches
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    prop.steps(psi, K, dt, m, A=A[W:W + K])
+    e1.record(stream)
+    barrier()
+    launches = prop.kernel_launches - l0
+    clk = clocks.stop()
+    t = max_over_ranks(e0.elapsed_time(e1) / 1e3)
+    result = psi.clone()
+    prop.profile(True)
+    info = prop.steps(psi, K, dt, m, A=A[W + K:W + 2 * K], info=True)
+    prof = prop.profile_read()
+    prop.profile(False)
+    host = torch.from_numpy(psi.cpu().numpy()).pin_memory()
+    Ke = max(3, min(K, 200))
+    barrier()
+    w0 = time.perf_counter()
+    for n in range(Ke):
+        prop.propagate_host(host, 1, dt, m, A=A[W + (n % K):W + (n % K) + 1])
+    te = max_over_ranks(time.perf_counter() - w0)
+    return dict(t=t, launches=launches, clocks=clk, result=result, info=info, prof=prof,
+                te=te, Ke=Ke)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -189,101 +258,96 @@ def run_ours(args):
     psi0 = wl.positive_energy_packet(g, p0=CFG["p0"], sigma_x=CFG["sigma_x"])
     K, W = args.steps, args.warmup
     A = pulse_schedule(0.0, dt, W + 2 * K, pulse.a0, pulse.omega, pulse.duration)
-    prop = Propagator(g.nx, g.ny, g.dx, g.dy, m_max=m)
-    prop.set_fields(None, A=(0.0, 0.0))
-    psi = torch.from_numpy(psi0).cuda()
-    stream = torch.cuda.current_stream()
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    # warm-up
-    prop.steps(psi, W, dt, m, A=A[:W])
-    barrier()
-    # timed region: K steps, device time by CUDA events on the launching stream
-    clocks = ClockSampler(local)
-    clocks.start()
-    l0 = prop.kernel_launches
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    e0.record(stream)
-    prop.steps(psi, K, dt, m, A=A[W:W + K])
-    e1.record(stream)
-    barrier()
-    launches = prop.kernel_launches - l0
-    clk = clocks.stop()
-    t = e0.elapsed_time(e1) / 1e3
-    if world > 1:
-        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
-    value = world * g.n_sites * m * K / t
-
-    # per-kernel device durations inside a second timed run of the same K steps
-    prop.profile(True)
-    info0 = prop.steps(psi, K, dt, m, A=A[W + K:W + 2 * K], info=True)
-    prof = prop.profile_read()
-    prop.profile(False)
-    pass_ms, pass_n = prof["pass"]
-    rec_ms, rec_n = prof["recombine"]
-    pass_avg = pass_ms / pass_n / 1e3
     pk = peaks()
-    # FP64 ALU roof: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
-    fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12
-    flops = PASS_FLOPS_PER_SITE * g.n_sites / pass_avg / 1e12
     hbm_peak = pk.get("hbm_gbs", 6800.0)
-    gbs = PASS_BYTES_PER_SITE * g.n_sites / pass_avg / 1e9
-    roofline = {"bound": "alu", "achieved": flops, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": flops / fp64_peak, "traffic": None,
-                "kernel": "lanczos_pass", "kernel_avg_us": pass_avg * 1e6,
-                "kernel_share": pass_ms / (pass_ms + rec_ms),
-                "peak_source": "derived FP64 FMA rate (probe: 1.19 TFLOP/s measured)"}
-    hbm = {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-           "bytes_per_site": PASS_BYTES_PER_SITE,
-           "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in pk else "fallback"}
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs (burst copy)" if "hbm_gbs" in pk else "fallback 6.8 TB/s"
+    runs = {}
+    for prec in ((args.only,) if args.only else ("fp64", "mixed")):
+        prop = Propagator(g.nx, g.ny, g.dx, g.dy, m_max=m, precision=prec)
+        prop.set_fields(None, A=(0.0, 0.0))
+        psi = torch.from_numpy(psi0).cuda()
+        runs[prec] = measure(prop, psi, A, K, W, world, dist, torch, local)
+        prop.close()
+        del psi
 
-    # end to end through the host-buffer C-ABI call: pinned H2D + step + D2H per step
-    host = torch.from_numpy(psi.cpu().numpy()).pin_memory()
-    Ke = max(3, min(K, 200))
-    barrier()
-    w0 = time.perf_counter()
-    for n in range(Ke):
-        prop.propagate_host(host, 1, dt, m, A=A[W + (n % K):W + (n % K) + 1])
-    w1 = time.perf_counter()
-    te = w1 - w0
-    if world > 1:
-        tt = torch.tensor([te], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        te = float(tt.item())
+    def site_rate(t, steps):
+        return world * g.n_sites * m * steps / t
+
+    def kernel_stats(r):
+        pass_ms, pass_n = r["prof"]["pass"]
+        rec_ms, rec_n = r["prof"]["recombine"]
+        return pass_ms / pass_n / 1e3, pass_ms / (pass_ms + rec_ms), rec_ms / max(1, rec_n) / 1e3
+
+    if args.only:
+        r = runs[args.only]
+        if rank == 0:
+            print(json.dumps({"partial": args.only, "ms_per_step": 1e3 * r["t"] / K,
+                              "value": site_rate(r["t"], K), "unit": UNIT}), flush=True)
+        return 0
     bytes_step = g.n_sites * SITE_BYTES
-    e2e = {"value": world * g.n_sites * m * Ke / te, "unit": UNIT,
-           "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": bytes_step,
-           "steps": Ke, "api": "dirac_propagate_host (pinned host buffer, 1 step per call)"}
-
+    # FP64 path: bound by the FP64 pipe
+    f = runs["fp64"]
+    f_pass, f_share, f_rec = kernel_stats(f)
+    fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12   # TFLOP/s, see the design doc
+    flops = PASS_FLOPS_PER_SITE * g.n_sites / f_pass / 1e12
+    roofline = {"bound": "alu", "achieved": flops, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": flops / fp64_peak, "traffic": traffic_for("fp64"),
+                "kernel": "lanczos_pass<double>", "kernel_avg_us": f_pass * 1e6,
+                "kernel_share": f_share,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz "
+                               "(probe measured 1.19 TFLOP/s)"}
+    f_gbs = PASS_BYTES_PER_SITE * g.n_sites / f_pass / 1e9
+    # mixed path: bound by HBM
+    x = runs["mixed"]
+    x_pass, x_share, x_rec = kernel_stats(x)
+    x_gbs = PASS_BYTES_PER_SITE_MIXED * g.n_sites / x_pass / 1e9
+    err = float(torch.linalg.vector_norm(x["result"] - f["result"]) /
+                torch.linalg.vector_norm(f["result"]))
+    mixed = {"value": site_rate(x["t"], K), "unit": UNIT, "ms_per_step": 1e3 * x["t"] / K,
+             "dtype": "f32 stencil/basis + f64 scalars and state",
+             "roofline": {"bound": "hbm", "achieved": x_gbs, "peak": hbm_peak, "unit": "GB/s",
+                          "frac": x_gbs / hbm_peak, "traffic": traffic_for("mixed"),
+                          "kernel": "lanczos_pass<float>", "kernel_avg_us": x_pass * 1e6,
+                          "kernel_share": x_share, "peak_source": hbm_src,
+                          "bytes_per_site": PASS_BYTES_PER_SITE_MIXED},
+             "error_vs_fp64": {"rel_l2": err, "per_unit_time": err / (K * dt),
+                               "steps": K, "simulated_time": K * dt},
+             "e2e": {"value": site_rate(x["te"], x["Ke"]), "unit": UNIT,
+                     "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": bytes_step,
+                     "steps": x["Ke"]},
+             "gpu_launches": x["launches"], "clocks": x["clocks"],
+             "recombine_avg_us": x_rec * 1e6,
+             "speedup_vs_fp64": f["t"] / x["t"]}
     line = None
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
-                "warmup": W, "ms_per_step": 1e3 * t / K, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        line = {"metric": METRIC, "value": site_rate(f["t"], K), "unit": UNIT, "n_gpus": world,
+                "steps": K, "warmup": W, "ms_per_step": 1e3 * f["t"] / K,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
                 "config": {"workload": CFG["name"], "grid": "%dx%d" % (g.nx, g.ny),
                            "dx": g.dx, "m": m, "dt": dt, "order": 2, "boundary": "periodic",
                            "pulse": "A_x = 50 sin^2(pi t) sin(0.05 t), T = 1",
-                           "l2": "inputs larger than L2: Krylov basis %.0f MB per step"
+                           "l2": "inputs larger than L2: Krylov basis %.0f MB (FP64) per step"
                                  % (m * g.n_sites * SITE_BYTES / 1e6),
                            "parallelism": "replicas" if world > 1 else "single GPU"},
-                "roofline": roofline, "hbm": hbm, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk,
-                "diagnostics": {"k_used": info0.k_used, "err_est_last": info0.err_est,
-                                "cum_err_est": info0.cum_err, "energy": info0.energy,
-                                "recombine_avg_us": rec_ms / max(1, rec_n) * 1e3}}
+                "roofline": roofline,
+                "hbm": {"achieved": f_gbs, "peak": hbm_peak, "unit": "GB/s",
+                        "frac": f_gbs / hbm_peak, "bytes_per_site": PASS_BYTES_PER_SITE,
+                        "peak_source": hbm_src},
+                "e2e": {"value": site_rate(f["te"], f["Ke"]), "unit": UNIT,
+                        "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": bytes_step,
+                        "steps": f["Ke"],
+                        "api": "dirac_propagate_host (pinned host buffer, 1 step per call)"},
+                "gpu_launches": f["launches"], "clocks": f["clocks"],
+                "mixed": mixed,
+                "diagnostics": {"k_used": f["info"].k_used, "err_est_last": f["info"].err_est,
+                                "cum_err_est": f["info"].cum_err, "energy": f["info"].energy,
+                                "recombine_avg_us": f_rec * 1e6}}
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline()
         elif not args.no_cpu_baseline:
             line["cpu_baseline"] = None
         print(json.dumps(line), flush=True)
-    prop.close()
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()

@@ -44,7 +44,7 @@ typedef enum {
 } dirac_status;
 
 enum { DIRAC_PERIODIC = 0, DIRAC_DIRICHLET = 1 };
-enum { DIRAC_FP64 = 0 };
+enum { DIRAC_FP64 = 0, DIRAC_MIXED = 1 };
 
 /* Largest Krylov dimension m one step may use. */
 #define DIRAC_KRYLOV_MAX 32
@@ -68,9 +68,14 @@ typedef struct {
  * particle mass and speed of light c (atomic units), central finite
  * differences of stencil_order 2 or 4 (Sec. 7: finite differences; the
  * central form keeps H Hermitian), DIRAC_PERIODIC or DIRAC_DIRICHLET
- * boundaries, precision DIRAC_FP64, and Krylov dimension up to m_max
- * (1..DIRAC_KRYLOV_MAX).  Allocates the workspace: (m_max + 1) device fields
- * of nx*ny sites.  cuda_stream is a cudaStream_t (NULL: the legacy default
+ * boundaries, precision DIRAC_FP64 or DIRAC_MIXED, and Krylov dimension up
+ * to m_max (1..DIRAC_KRYLOV_MAX).  DIRAC_FP64 computes everything in FP64.
+ * DIRAC_MIXED keeps the state psi in complex128 but stores the Krylov basis
+ * in complex64 and applies H in FP32, while the inner products are summed in
+ * FP64 across warps and the scalars alpha, beta, the small exponential and
+ * the recombination coefficients stay FP64; the recombination adds C_1 psi
+ * in FP64.  Allocates the workspace: (m_max + 1) device fields of nx*ny
+ * sites (32 B per site for FP64, 16 B for MIXED).  cuda_stream is a cudaStream_t (NULL: the legacy default
  * stream).  On success *out owns the context.
  * Errors: DIRAC_EINVAL (nx, ny < 1; dx, dy, c <= 0; mass < 0; bad order,
  * boundary, precision or m_max), DIRAC_ENOMEM, DIRAC_ECUDA.

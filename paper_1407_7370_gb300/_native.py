@@ -19,7 +19,7 @@ KERNEL_KINDS = 2
 
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ESTATE = range(6)
 PERIODIC, DIRICHLET = 0, 1
-FP64 = 0
+FP64, MIXED = 0, 1
 
 
 class StepInfoC(ctypes.Structure):

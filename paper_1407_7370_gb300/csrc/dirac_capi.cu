@@ -10,8 +10,10 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
+#include <utility>
 #include <vector>
 
 using namespace dirac;
@@ -62,10 +64,10 @@ struct dirac_ctx {
   double dx = 0, dy = 0, mass = 1, c = 137.036;
   cudaStream_t stream = nullptr;
   long long n_sites = 0;
-  vec4* basis = nullptr;          // q^_2 .. q^_m
-  vec4* ybuf[2] = {nullptr, nullptr};
+  void* basis = nullptr;          // q^_2 .. q^_m (complex128, or complex64 when mixed)
+  void* ybuf[2] = {nullptr, nullptr};
   vec4* psi_own = nullptr;        // staging for the host-buffer call
-  double* V = nullptr;
+  void* V = nullptr;              // double, or float when mixed
   bool has_v = false;
   double vmin = 0, vmax = 0;
   double ax = 0, ay = 0, shift = 0;
@@ -132,21 +134,72 @@ dirac_status make_cheb(double c0, double half, double dt, double shift, ChebPara
   return DIRAC_OK;
 }
 
-template <int R, bool D, bool V>
-cudaError_t launch_pass_t(const PassParams& p, dim3 grid, cudaStream_t s) {
-  lanczos_pass<R, D, V><<<grid, NT, 0, s>>>(p);
-  return cudaGetLastError();
+// Launch with programmatic stream serialisation: the kernel may be scheduled
+// while the previous kernel in the stream finishes; it waits for it (and sees
+// its writes) at its griddepcontrol.wait.
+// DIRAC_NO_PDL=1 in the environment turns the overlap off (debugging aid).
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* v = std::getenv("DIRAC_NO_PDL");
+    return !(v && v[0] == '1');
+  }();
+  return on;
 }
 
-cudaError_t launch_pass(const dirac_ctx* c, const PassParams& p) {
+template <class... KArgs, class... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+// Persistent launch: as many CTAs as fit on the GPU at once (never more than
+// there are tiles); each CTA walks the tiles with a grid stride.
+template <class S, int R, bool D, bool V, bool Q64>
+cudaError_t launch_pass_t(const PassParams& p, int n_sm, cudaStream_t s) {
+  static int occ = 0;
+  if (occ == 0) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lanczos_pass<S, R, D, V, Q64>, NTP, 0);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+  }
+  // FP32 (memory-bound): equal work per CTA, T = ceil(tiles / resident CTAs)
+  // tiles each; FP64 (FP64-pipe-bound): fill every slot to hide latency
+  const int slots = std::max(1, n_sm * occ);
+  const int per = (p.ntiles + slots - 1) / slots;
+  const int grid = sizeof(S) == sizeof(float) ? std::max(1, (p.ntiles + per - 1) / per)
+                                              : std::max(1, std::min(p.ntiles, slots));
+  return launch_pdl(lanczos_pass<S, R, D, V, Q64>, grid, NTP, s, p);
+}
+
+template <class S, bool Q64>
+cudaError_t launch_pass_s(const dirac_ctx* c, const PassParams& p) {
   const bool d = c->boundary == DIRAC_DIRICHLET, v = c->has_v;
   if (c->order == 2) {
-    if (d) return v ? launch_pass_t<1, true, true>(p, c->grid, c->stream) : launch_pass_t<1, true, false>(p, c->grid, c->stream);
-    return v ? launch_pass_t<1, false, true>(p, c->grid, c->stream) : launch_pass_t<1, false, false>(p, c->grid, c->stream);
+    if (d) return v ? launch_pass_t<S, 1, true, true, Q64>(p, c->n_sm, c->stream) : launch_pass_t<S, 1, true, false, Q64>(p, c->n_sm, c->stream);
+    return v ? launch_pass_t<S, 1, false, true, Q64>(p, c->n_sm, c->stream) : launch_pass_t<S, 1, false, false, Q64>(p, c->n_sm, c->stream);
   }
-  if (d) return v ? launch_pass_t<2, true, true>(p, c->grid, c->stream) : launch_pass_t<2, true, false>(p, c->grid, c->stream);
-  return v ? launch_pass_t<2, false, true>(p, c->grid, c->stream) : launch_pass_t<2, false, false>(p, c->grid, c->stream);
+  if (d) return v ? launch_pass_t<S, 2, true, true, Q64>(p, c->n_sm, c->stream) : launch_pass_t<S, 2, true, false, Q64>(p, c->n_sm, c->stream);
+  return v ? launch_pass_t<S, 2, false, true, Q64>(p, c->n_sm, c->stream) : launch_pass_t<S, 2, false, false, Q64>(p, c->n_sm, c->stream);
 }
+
+// FP64 path: everything complex128.  Mixed path: passes 1 and 2 read the
+// complex128 state as q^_1, later passes read complex64 basis vectors.
+cudaError_t launch_pass(const dirac_ctx* c, const PassParams& p) {
+  if (c->precision == DIRAC_FP64) return launch_pass_s<double, true>(c, p);
+  if (p.pass <= 2) return launch_pass_s<float, true>(c, p);
+  return launch_pass_s<float, false>(c, p);
+}
+
+size_t site_bytes(int precision) { return precision == DIRAC_FP64 ? sizeof(double4_32a) : sizeof(float4); }
 
 bool aligned32(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 31u) == 0; }
 
@@ -181,6 +234,8 @@ dirac_status enqueue_step(dirac_ctx* c, vec4* psi, double dt, int m, double tol)
   p.partials = c->partials;
   p.nx = c->nx;
   p.ny = c->ny;
+  p.tiles_x = c->grid.x;
+  p.ntiles = c->grid.x * c->grid.y;
   p.m = m;
   p.kx = c->c / (kfac * c->dx);
   p.ky = c->c / (kfac * c->dy);
@@ -190,7 +245,11 @@ dirac_status enqueue_step(dirac_ctx* c, vec4* psi, double dt, int m, double tol)
   p.shift = c->shift;
   p.dt = dt;
   p.tol = tol;
+  p.kxf = (float)p.kx; p.kyf = (float)p.ky; p.cAxf = (float)p.cAx; p.cAyf = (float)p.cAy;
+  p.probe_coef = make_coef(1.0, 0.0, 0.0, p.mcc - p.shift, -p.mcc - p.shift);
   const long long n = c->n_sites;
+  const size_t sb = site_bytes(c->precision);
+  char* basis = static_cast<char*>(c->basis);
   if (c->need_probe) {
     p.pass = 1;
     p.probe = 1;
@@ -203,8 +262,8 @@ dirac_status enqueue_step(dirac_ctx* c, vec4* psi, double dt, int m, double tol)
   for (int i = 1; i <= m; ++i) {
     p.pass = i;
     p.y_prev = (i >= 2) ? c->ybuf[(i - 1) & 1] : nullptr;
-    p.q_prev = (i == 2) ? psi : (i >= 3 ? c->basis + (size_t)(i - 3) * n : nullptr);
-    p.q_out = (i >= 2) ? c->basis + (size_t)(i - 2) * n : nullptr;
+    p.q_prev = (i == 2) ? (const void*)psi : (i >= 3 ? (const void*)(basis + (size_t)(i - 3) * n * sb) : nullptr);
+    p.q_out = (i >= 2) ? (void*)(basis + (size_t)(i - 2) * n * sb) : nullptr;
     p.y_out = (i < m) ? c->ybuf[i & 1] : nullptr;
     CUDA_TRY(mark(c, KIND_PASS));
     CUDA_TRY(launch_pass(c, p));
@@ -212,8 +271,10 @@ dirac_status enqueue_step(dirac_ctx* c, vec4* psi, double dt, int m, double tol)
   }
   const int rb = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, (long long)c->n_sm * 8));
   CUDA_TRY(mark(c, KIND_RECOMBINE));
-  recombine<<<rb, 256, 0, c->stream>>>(psi, c->basis, n, c->st);
-  CUDA_TRY(cudaGetLastError());
+  if (c->precision == DIRAC_FP64)
+    CUDA_TRY(launch_pdl(recombine, rb, 256, c->stream, psi, static_cast<const vec4*>(c->basis), n, c->st));
+  else
+    CUDA_TRY(launch_pdl(recombine_mixed, rb, 256, c->stream, psi, static_cast<const float4*>(c->basis), n, c->st));
   ++c->launches;
   CUDA_TRY(mark(c, KIND_END));
   return DIRAC_OK;
@@ -273,6 +334,11 @@ dirac_status run_steps(dirac_ctx* c, vec4* psi, int nsteps, double dt, int m, do
   return DIRAC_OK;
 }
 
+__global__ void to_float_kernel(const double* in, float* out, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
 __global__ void minmax_kernel(const double* v, long long n, double* out) {
   __shared__ double smin[256], smax[256];
   double lo = 1e308, hi = -1e308;
@@ -326,7 +392,8 @@ dirac_status dirac_create(dirac_ctx** out, int nx, int ny, double dx, double dy,
   if (!(mass >= 0) || !std::isfinite(mass)) return fail(DIRAC_EINVAL, "mass must be finite and >= 0");
   if (stencil_order != 2 && stencil_order != 4) return fail(DIRAC_EINVAL, "stencil_order must be 2 or 4");
   if (boundary != DIRAC_PERIODIC && boundary != DIRAC_DIRICHLET) return fail(DIRAC_EINVAL, "bad boundary");
-  if (precision != DIRAC_FP64) return fail(DIRAC_EINVAL, "precision must be DIRAC_FP64");
+  if (precision != DIRAC_FP64 && precision != DIRAC_MIXED)
+    return fail(DIRAC_EINVAL, "precision must be DIRAC_FP64 or DIRAC_MIXED");
   if (m_max < 1 || m_max > DIRAC_KRYLOV_MAX) return fail(DIRAC_EINVAL, "m_max must be 1..%d", DIRAC_KRYLOV_MAX);
   const long long n = (long long)nx * ny;
   if (n > (1LL << 31)) return fail(DIRAC_EINVAL, "grid too large");
@@ -336,11 +403,11 @@ dirac_status dirac_create(dirac_ctx** out, int nx, int ny, double dx, double dy,
   ctx->nx = nx; ctx->ny = ny; ctx->dx = dx; ctx->dy = dy; ctx->mass = mass; ctx->c = c;
   ctx->order = stencil_order; ctx->boundary = boundary; ctx->precision = precision;
   ctx->m_max = m_max; ctx->stream = (cudaStream_t)cuda_stream; ctx->n_sites = n;
-  ctx->grid = dim3((nx + TX - 1) / TX, (ny + TY - 1) / TY);
+  ctx->grid = dim3((nx + TILE - 1) / TILE, (ny + TILE - 1) / TILE);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, dev);
-  const size_t vb = (size_t)n * sizeof(vec4);
+  const size_t vb = (size_t)n * site_bytes(precision);
   const int nbasis = std::max(1, m_max - 1);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->basis, vb * nbasis);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->ybuf[0], vb);
@@ -394,11 +461,18 @@ dirac_status dirac_set_fields(dirac_ctx* ctx, const double* V_dev, double A_x, d
   if (!std::isfinite(A_x) || !std::isfinite(A_y) || !std::isfinite(energy_shift))
     return fail(DIRAC_EINVAL, "non-finite field scalar");
   if (V_dev) {
-    if (!ctx->V) CUDA_TRY(cudaMalloc(&ctx->V, sizeof(double) * ctx->n_sites));
-    CUDA_TRY(cudaMemcpyAsync(ctx->V, V_dev, sizeof(double) * ctx->n_sites, cudaMemcpyDeviceToDevice, ctx->stream));
+    const bool f32 = ctx->precision != DIRAC_FP64;
+    if (!ctx->V) CUDA_TRY(cudaMalloc(&ctx->V, (f32 ? sizeof(float) : sizeof(double)) * ctx->n_sites));
+    if (f32) {
+      to_float_kernel<<<256, 256, 0, ctx->stream>>>(V_dev, static_cast<float*>(ctx->V), ctx->n_sites);
+      ++ctx->launches;
+      CUDA_TRY(cudaGetLastError());
+    } else {
+      CUDA_TRY(cudaMemcpyAsync(ctx->V, V_dev, sizeof(double) * ctx->n_sites, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
     double* mm = nullptr;
     CUDA_TRY(cudaMalloc(&mm, 2 * sizeof(double)));
-    minmax_kernel<<<1, 256, 0, ctx->stream>>>(ctx->V, ctx->n_sites, mm);
+    minmax_kernel<<<1, 256, 0, ctx->stream>>>(V_dev, ctx->n_sites, mm);
     ++ctx->launches;
     double h[2];
     cudaError_t e = cudaGetLastError();
@@ -632,7 +706,7 @@ extern "C" dirac_status dirac_lanczos_step_noalloc(const dirac_problem* pb, void
 
   // scratch layout: DevState | partials | y^[2] | basis[m-1]
   const long long n = (long long)nx * ny;
-  const dim3 grid((nx + TX - 1) / TX, (ny + TY - 1) / TY);
+  const dim3 grid((nx + TILE - 1) / TILE, (ny + TILE - 1) / TILE);
   const size_t ncta = (size_t)grid.x * grid.y;
   const size_t field = round256((size_t)n * sizeof(vec4));
   const size_t off_part = round256(sizeof(DevState));
@@ -691,6 +765,8 @@ extern "C" dirac_status dirac_lanczos_step_noalloc(const dirac_problem* pb, void
   p.partials = partials;
   p.nx = nx;
   p.ny = ny;
+  p.tiles_x = grid.x;
+  p.ntiles = grid.x * grid.y;
   p.m = m;
   p.kx = pb->c / (kfac * pb->dx);
   p.ky = pb->c / (kfac * pb->dy);
@@ -700,10 +776,16 @@ extern "C" dirac_status dirac_lanczos_step_noalloc(const dirac_problem* pb, void
   p.shift = pb->energy_shift;
   p.dt = dt;
   p.tol = tol;
+  p.kxf = (float)p.kx; p.kyf = (float)p.ky; p.cAxf = (float)p.cAx; p.cAyf = (float)p.cAy;
+  p.probe_coef = make_coef(1.0, 0.0, 0.0, p.mcc - p.shift, -p.mcc - p.shift);
 
+  int n_sm = 0, dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
   dirac_ctx view;   // launch configuration only; owns nothing
   view.nx = nx; view.ny = ny; view.order = pb->stencil_order; view.boundary = pb->boundary;
   view.has_v = pb->V_dev != nullptr; view.grid = grid; view.stream = stream;
+  view.precision = DIRAC_FP64; view.n_sm = n_sm;
   p.pass = 1;
   p.probe = 1;
   CUDA_TRY(launch_pass(&view, p));
@@ -711,17 +793,13 @@ extern "C" dirac_status dirac_lanczos_step_noalloc(const dirac_problem* pb, void
   for (int i = 1; i <= m; ++i) {
     p.pass = i;
     p.y_prev = (i >= 2) ? ybuf[(i - 1) & 1] : nullptr;
-    p.q_prev = (i == 2) ? psi : (i >= 3 ? basis + (size_t)(i - 3) * n : nullptr);
-    p.q_out = (i >= 2) ? basis + (size_t)(i - 2) * n : nullptr;
-    p.y_out = (i < m) ? ybuf[i & 1] : nullptr;
+    p.q_prev = (i == 2) ? (const void*)psi : (i >= 3 ? (const void*)(basis + (size_t)(i - 3) * n) : nullptr);
+    p.q_out = (i >= 2) ? (void*)(basis + (size_t)(i - 2) * n) : nullptr;
+    p.y_out = (i < m) ? (void*)ybuf[i & 1] : nullptr;
     CUDA_TRY(launch_pass(&view, p));
   }
-  int n_sm = 0, dev = 0;
-  CUDA_TRY(cudaGetDevice(&dev));
-  CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
   const int rb = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, (long long)n_sm * 8));
-  recombine<<<rb, 256, 0, stream>>>(psi, basis, n, st);
-  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(launch_pdl(recombine, rb, 256, stream, psi, (const vec4*)basis, n, st));
 
   if (info) {
     DevState h;

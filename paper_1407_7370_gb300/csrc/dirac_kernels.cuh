@@ -32,21 +32,42 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cuda/atomic>
+
 namespace dirac {
 
 constexpr int KMAX = 32;        // Krylov dimension limit (one warp holds T)
 constexpr int CHEB_MAX = 160;   // Chebyshev terms limit
-constexpr int TX = 32;          // tile width (sites, x)
-constexpr int TY = 8;           // tile height (sites, y)
-constexpr int NT = TX * TY;     // threads per tile CTA
 constexpr int ERR_NONFINITE = 4;
 
 using vec4 = double4_32a;       // one site: (u.re, u.im, d.re, d.im)
 
+// Coefficients one pass needs, prepared by the finisher of the pass before
+// (FP64 values and FP32 copies, so that no thread converts on the FP64 pipe).
+struct PassCoef {
+  double g, gd, e, au0, ad0;          // q^ = g y^ - gd q^_prev; y^ -= e q^_prev; diagonals
+  float gf, gdf, ef, au_hi, au_lo, ad_hi, ad_lo, pad;
+};
+
+__host__ __device__ inline PassCoef make_coef(double g, double gd, double e, double au0, double ad0) {
+  PassCoef c;
+  c.g = g; c.gd = gd; c.e = e; c.au0 = au0; c.ad0 = ad0;
+  c.gf = (float)g; c.gdf = (float)gd; c.ef = (float)e;
+  // the diagonals (up to ~2 m c^2) as a rounded float plus its remainder, so
+  // that on the FP32 path their rounding does not act as a constant
+  // perturbation of the mass term
+  c.au_hi = (float)au0; c.au_lo = (float)(au0 - (double)c.au_hi);
+  c.ad_hi = (float)ad0; c.ad_lo = (float)(ad0 - (double)c.ad_hi);
+  c.pad = 0.f;
+  return c;
+}
+
 struct DevState {
+  PassCoef pc[KMAX + 2];    // coefficients of pass i (pc[1]: first pass of a step)
   double alpha[KMAX + 2];   // T diagonal of H - s, index 1..k
   double beta[KMAX + 2];    // beta[i] couples i and i+1; beta[k] = beta_k estimate
   double nu[KMAX + 2];      // ||q^_i||
+  double inv_nu[KMAX + 2];  // 1 / ||q^_i||
   double sigma[KMAX + 2];   // stencil shift of pass i
   double g[KMAX + 2];
   double d[KMAX + 2];
@@ -70,18 +91,21 @@ struct ChebParams {
 };
 
 struct PassParams {
-  const vec4* psi;          // q^_1 (the state, read in place)
-  const vec4* y_prev;       // y^_{i-1}
-  const vec4* q_prev;       // q^_{i-1}
-  vec4* q_out;              // q^_i  (i >= 2)
-  vec4* y_out;              // y^_i  (NULL on the last pass)
-  const double* V;          // potential energy [ny][nx] or NULL
+  const void* psi;          // q^_1 (the FP64 state, read in place)
+  const void* y_prev;       // y^_{i-1}
+  const void* q_prev;       // q^_{i-1}
+  void* q_out;              // q^_i  (i >= 2)
+  void* y_out;              // y^_i  (NULL on the last pass)
+  const void* V;            // potential energy [ny][nx] (double) or NULL
   DevState* st;
   double* partials;         // 3 doubles per CTA
   int nx, ny;
+  int tiles_x, ntiles;      // tiles of TILE x TILE sites (grid-stride over them)
   int pass, m, probe;
   double kx, ky;            // c/(2dx) (order 2) or c/(12dx) (order 4)
   double mcc, cAx, cAy, shift, dt, tol;
+  float kxf, kyf, cAxf, cAyf; // the same four in FP32 (rounded on the host)
+  PassCoef probe_coef;      // coefficients of the probe pass (shift 0)
   ChebParams cheb;
 };
 
@@ -111,15 +135,16 @@ __device__ __forceinline__ int wrap(int g, int n, bool& outside) {
 // R = half * dt is sum_n eps_n (-i)^n J_n(R) T_n(X) (Jacobi-Anger), summed
 // with the three-term Chebyshev recurrence T_{n+1} = 2 X T_n - T_{n-1}.
 // ---------------------------------------------------------------------------
-__device__ void cheb_expm_e1(const ChebParams& cp, int k, const volatile double* alpha,
-                             const volatile double* beta, double& vr, double& vi) {
+__device__ void cheb_expm_e1(const ChebParams& cp, int k, double alpha_j, double beta_lo,
+                             double beta_hi, double& vr, double& vi) {
+  // lane j holds alpha_{j+1} and the couplings to its neighbours (0 outside)
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   double a = 0.0, bl = 0.0, bh = 0.0;
   if (lane < k) {
-    a = (alpha[lane + 1] - cp.c0) * cp.inv_half;
-    if (lane >= 1) bl = beta[lane] * cp.inv_half;
-    if (lane + 1 < k) bh = beta[lane + 1] * cp.inv_half;
+    a = (alpha_j - cp.c0) * cp.inv_half;
+    if (lane >= 1) bl = beta_lo * cp.inv_half;
+    if (lane + 1 < k) bh = beta_hi * cp.inv_half;
   }
   double t0 = (lane == 0) ? 1.0 : 0.0;
   double up = __shfl_up_sync(full, t0, 1);
@@ -143,18 +168,26 @@ __device__ void cheb_expm_e1(const ChebParams& cp, int k, const volatile double*
 
 // ---------------------------------------------------------------------------
 // Scalar update after pass i: run by warp 0 of the last CTA with the grid
-// totals P, Y, X in every lane.
+// totals P, Y, X in every lane.  Values written by earlier launches are read
+// with plain loads up front; new values travel by shuffles.  rsqrt gives
+// sqrt(X), 1/X, sqrt(s2) and 1/sqrt(s2) with few dependent FP64 operations.
 // ---------------------------------------------------------------------------
 __device__ void finish_pass(const PassParams& p, double P, double Y, double X) {
-  volatile DevState* st = p.st;
+  DevState* st = p.st;
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int i = p.pass;
   const bool ok = isfinite(P) && isfinite(Y) && isfinite(X) && X > 0.0;
   if (p.probe) {   // Rayleigh quotient of psi: the first stencil shift
     if (lane == 0) {
-      if (ok) { st->sigma[1] = st->sigma[1] + P / X; st->sigma_valid = 1; }
-      else { st->error = ERR_NONFINITE; st->stopped = 1; }
+      if (ok) {
+        const double s1 = P / X;   // the probe ran with shift 0
+        st->sigma[1] = s1;
+        st->pc[1] = make_coef(1.0, 0.0, 0.0, p.mcc - p.shift - s1, -p.mcc - p.shift - s1);
+        st->sigma_valid = 1;
+      } else {
+        st->error = ERR_NONFINITE; st->stopped = 1;
+      }
     }
     return;
   }
@@ -162,68 +195,82 @@ __device__ void finish_pass(const PassParams& p, double P, double Y, double X) {
     if (lane == 0) { st->error = ERR_NONFINITE; st->stopped = 1; }
     return;
   }
-  int stop = 0, brk = 0;
-  double beta_hat = 0.0;
+  // earlier T entries (lane j: component j+1), issued before the scalar chain
+  const double a_old = (lane + 1 < i) ? st->alpha[lane + 1] : 0.0;
+  const double b_old = (lane + 2 < i) ? st->beta[lane + 1] : 0.0;   // exact beta_{j+1}
+  const double invnu_old = (lane + 1 < i) ? st->inv_nu[lane + 1] : 0.0;
+  const double sigma = st->sigma[i];
+  const double scale_old = (i == 1) ? 0.0 : st->scale;
+  const double bhat_prev = (i == 1) ? 0.0 : st->beta[i - 1];       // estimate from pass i-1
+  const double nu1_old = (i == 1) ? 0.0 : st->nu[1];
+  const double psi_norm_old = st->psi_norm, cum_old = st->cum_err;
+
+  // scalar chain (every lane computes it; no broadcast needed)
+  const double y = rsqrt(X);            // 1 / nu_i
+  const double nu = X * y;
+  const double rX = y * y;
+  const double dd = P * rX;             // alpha_i - sigma_i
+  const double alpha = sigma + dd;
+  const double s2 = fma(-P, dd, Y);     // nu_i^2 beta_i^2 (estimate)
+  const double rs = s2 > 0.0 ? rsqrt(s2) : 0.0;
+  const double sq = s2 > 0.0 ? s2 * rs : 0.0;
+  const double beta_hat = sq * y;
+  const double bprev = nu * bhat_prev;  // exact beta_{i-1} from the measured norm
+  double scale = fmax(scale_old, fabs(alpha + p.shift));
+  if (i > 1) scale = fmax(scale, bprev);
+  const int brk = beta_hat <= 1e-12 * scale;
+  int stop = (i >= p.m) || brk;
+  const double nu1 = (i == 1) ? nu : nu1_old;
+  const double psi_norm = (i == 1) ? nu : psi_norm_old;
   if (lane == 0) {
-    const double nu = sqrt(X);
-    const double dd = P / X;
-    const double alpha = st->sigma[i] + dd;
     st->nu[i] = nu;
+    st->inv_nu[i] = y;
     st->alpha[i] = alpha;
     st->d[i] = dd;
-    double scale = (i == 1) ? 0.0 : st->scale;
-    if (i == 1) {
-      st->psi_norm = nu;
-      st->energy = alpha + p.shift;
-    } else {
-      const double b = nu / (st->g[i - 1] * st->nu[i - 1]);
-      st->beta[i - 1] = b;
-      scale = fmax(scale, b);
-    }
-    scale = fmax(scale, fabs(alpha + p.shift));
-    st->scale = scale;
-    const double s2 = Y - P * dd;
-    const double sq = s2 > 0.0 ? sqrt(s2) : 0.0;
-    beta_hat = sq / nu;
     st->beta[i] = beta_hat;
-    if (s2 > 0.0) st->kappa_max = fmax(st->kappa_max, Y / s2);
-    brk = beta_hat <= 1e-12 * scale;
-    stop = (i >= p.m) || brk;
+    if (i > 1) st->beta[i - 1] = bprev;
+    st->scale = scale;
+    if (i == 1) { st->psi_norm = nu; st->energy = alpha + p.shift; }
+    if (s2 > 0.0) st->kappa_max = fmax(st->kappa_max, Y * rs * rs);
     if (!stop) {
-      st->g[i] = 1.0 / sq;
-      st->e[i + 1] = sq / X;
+      st->g[i] = rs;
+      st->e[i + 1] = sq * rX;
       st->sigma[i + 1] = alpha;
+      st->pc[i + 1] = make_coef(rs, rs * dd, sq * rX, p.mcc - p.shift - alpha, -p.mcc - p.shift - alpha);
     }
   }
-  stop = __shfl_sync(full, stop, 0);
-  brk = __shfl_sync(full, brk, 0);
-  beta_hat = __shfl_sync(full, beta_hat, 0);
-  __syncwarp();
+  // this lane's row of T^(i)
+  const double a_j = (lane + 1 == i) ? alpha : a_old;
+  const double b_hi = (lane + 2 == i) ? bprev : b_old;               // couples j+1, j+2
+  const double b_lo = __shfl_up_sync(full, b_hi, 1);                 // couples j, j+1
+  const double inv_nu_j = (lane + 1 == i) ? y : invnu_old;
   double vr = 0.0, vi = 0.0;
   bool have_v = false;
   if (!stop && p.tol > 0.0) {   // adaptive Krylov dimension (Sec. 4, Eq. 18)
-    cheb_expm_e1(p.cheb, i, st->alpha, st->beta, vr, vi);
+    cheb_expm_e1(p.cheb, i, a_j, b_lo, b_hi, vr, vi);
     have_v = true;
     const double vk = __shfl_sync(full, sqrt(vr * vr + vi * vi), i - 1);
     stop = (beta_hat * p.dt * vk <= p.tol);
   }
   if (!stop) return;
-  if (!have_v) cheb_expm_e1(p.cheb, i, st->alpha, st->beta, vr, vi);
+  if (!have_v) cheb_expm_e1(p.cheb, i, a_j, b_lo, b_hi, vr, vi);
   // C_j = nu_1 / nu_j * v_j applied to q^_j; Eq. 18 estimate from v_k
   const double vk = __shfl_sync(full, sqrt(vr * vr + vi * vi), i - 1);
   if (lane < i) {
-    const double f = st->nu[1] / st->nu[lane + 1];
+    const double f = nu1 * inv_nu_j;
     st->coef_re[lane + 1] = f * vr;
     st->coef_im[lane + 1] = f * vi;
   }
   if (lane == 0) {
-    const double err = p.dt * beta_hat * st->psi_norm * vk;
+    const double err = p.dt * beta_hat * psi_norm * vk;
     st->err_est = err;
-    st->cum_err = st->cum_err + err;
+    st->cum_err = cum_old + err;
     st->k_used = i;
     st->breakdown = brk;
     st->beta_last = beta_hat;
-    st->sigma[1] = st->alpha[1];   // next step's first shift
+    const double s1 = (i == 1) ? alpha : st->alpha[1];   // next step's first shift
+    st->sigma[1] = s1;
+    st->pc[1] = make_coef(1.0, 0.0, 0.0, p.mcc - p.shift - s1, -p.mcc - p.shift - s1);
     st->sigma_valid = 1;
     st->stopped = 1;
   }
@@ -231,167 +278,226 @@ __device__ void finish_pass(const PassParams& p, double P, double Y, double X) {
 
 // ---------------------------------------------------------------------------
 // One Lanczos iteration: stencil product with fused reductions.
-// R = stencil half width (1: order 2, 2: order 4).
+//
+// S    arithmetic type of the stencil (double: FP64 path; float: mixed path)
+// R    stencil half width (1: order 2, 2: order 4)
+// QIN64  q^_{i-1} (and psi) are complex128 (FP64 path, and passes 1-2 of the
+//      mixed path, whose q^_1 is the FP64 state itself); otherwise they are
+//      stored like y^ (complex64 in the mixed path)
+//
+// A CTA owns a TILE x TILE block of sites; thread (tx, tg) handles column tx
+// and rows tg, tg + NG, tg + 2 NG, tg + 3 NG (NG = TILE / RPT), so every warp
+// touches one contiguous row segment per access.  The tile and a cross-shaped
+// halo of q^_i are formed in shared memory from y^_{i-1} and q^_{i-1}.
 // ---------------------------------------------------------------------------
-template <int R, bool DIRI, bool HAS_V>
-__global__ void __launch_bounds__(NT) lanczos_pass(const __grid_constant__ PassParams p) {
-  __shared__ vec4 tile[TY + 2 * R][TX + 2 * R];
-  __shared__ double red[NT / 32][3];
+template <class S> struct Vec4;
+template <> struct Vec4<double> { using T = double4_32a; };
+template <> struct Vec4<float> { using T = float4; };
+
+template <class To, class From>
+__device__ __forceinline__ void cvt4(const From& a, To (&o)[4]) {
+  o[0] = (To)a.x; o[1] = (To)a.y; o[2] = (To)a.z; o[3] = (To)a.w;
+}
+
+template <class S>
+__device__ __forceinline__ S warp_sum_t(S v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+constexpr int TILE = 32;          // tile edge (sites)
+constexpr int RPT = 4;            // rows per thread
+constexpr int NG = TILE / RPT;    // row groups
+constexpr int NTP = 32 * NG;      // threads per CTA (256)
+
+template <class S, int R, bool DIRI, bool HAS_V, bool QIN64>
+__global__ void __launch_bounds__(NTP, sizeof(S) == sizeof(float) ? 5 : 2)
+lanczos_pass(const __grid_constant__ PassParams p) {
+  using T4 = typename Vec4<S>::T;           // storage of y^ and (if !QIN64) q^
+  constexpr int W = TILE + 2 * R;
+  __shared__ __align__(32) S tile[TILE + 2 * R][W][4];
+  __shared__ double red[NTP / 32][3];
   __shared__ int last_cta;
-  volatile DevState* st = p.st;
+  // programmatic dependent launch: everything above may overlap the tail of
+  // the previous kernel; nothing it wrote is read before this point
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const DevState* st = p.st;   // written by earlier launches: plain loads
   if (st->stopped) return;
-
   const int i = p.pass;
-  const double sigma = st->sigma[i];
-  double g = 1.0, gd = 0.0, e = 0.0;
-  if (i >= 2) {
-    g = st->g[i - 1];
-    gd = g * st->d[i - 1];
-    e = st->e[i];
-  }
+  const PassCoef pc = p.probe ? p.probe_coef : st->pc[i];
+  constexpr bool F32 = sizeof(S) == sizeof(float);
+  const S gS = F32 ? (S)pc.gf : (S)pc.g;
+  const S gdS = F32 ? (S)pc.gdf : (S)pc.gd;
+  const S eS = F32 ? (S)pc.ef : (S)pc.e;
   const int nx = p.nx, ny = p.ny;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int tx = threadIdx.x & 31, tg = threadIdx.x >> 5;
+  const T4* yprev = static_cast<const T4*>(p.y_prev);
+  const S kx = F32 ? (S)p.kxf : (S)p.kx, ky = F32 ? (S)p.kyf : (S)p.ky;
+  const S cAx = F32 ? (S)p.cAxf : (S)p.cAx, cAy = F32 ? (S)p.cAyf : (S)p.cAy;
+  const S au_hi = F32 ? (S)pc.au_hi : (S)pc.au0, au_lo = F32 ? (S)pc.au_lo : S(0);
+  const S ad_hi = F32 ? (S)pc.ad_hi : (S)pc.ad0, ad_lo = F32 ? (S)pc.ad_lo : S(0);
+  S accP = S(0), accY = S(0), accX = S(0);
+  int x0 = 0, y0 = 0;
 
-  // value of q^_i at grid point (gx, gy), possibly outside the grid
-  auto form = [&](int gx, int gy, vec4& qprev_out) -> vec4 {
+  // q^_i at grid point (gx, gy) (zero outside for Dirichlet) into smem slot
+  auto form = [&](int gx, int gy, int row, int col, S (&qp)[4]) {
     bool ox, oy;
     const int ix = wrap<DIRI>(gx, nx, ox), iy = wrap<DIRI>(gy, ny, oy);
-    vec4 v;
-    if (ox || oy) { v.x = v.y = v.z = v.w = 0.0; qprev_out = v; return v; }
-    const size_t idx = (size_t)iy * nx + ix;
-    if (i == 1) {
-      v = p.psi[idx];
-      qprev_out = v;
-    } else {
-      const vec4 yv = p.y_prev[idx];
-      const vec4 qv = p.q_prev[idx];
-      v.x = fma(-gd, qv.x, g * yv.x);
-      v.y = fma(-gd, qv.y, g * yv.y);
-      v.z = fma(-gd, qv.z, g * yv.z);
-      v.w = fma(-gd, qv.w, g * yv.w);
-      qprev_out = qv;
+    S q[4] = {S(0), S(0), S(0), S(0)};
+    qp[0] = qp[1] = qp[2] = qp[3] = S(0);
+    if (!(ox || oy)) {
+      const size_t idx = (size_t)iy * nx + ix;
+      if constexpr (QIN64) {
+        const double4_32a* qsrc = static_cast<const double4_32a*>(i == 1 ? p.psi : p.q_prev);
+        cvt4(qsrc[idx], qp);
+      } else {
+        cvt4(static_cast<const T4*>(p.q_prev)[idx], qp);
+      }
+      if (i == 1) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) q[c] = qp[c];
+      } else {
+        S yv[4];
+        cvt4(yprev[idx], yv);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) q[c] = fma(-gdS, qp[c], gS * yv[c]);
+      }
     }
-    return v;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) tile[row][col][c] = q[c];
   };
 
-  // centre slots: one per thread, keeping q^_{i-1} of the own site
-  vec4 qprev;
-  tile[ty + R][tx + R] = form(x0 + tx, y0 + ty, qprev);
-  // halo slots (cross shape, no corners)
-  constexpr int NH_ROW = 2 * R * TX, NH = NH_ROW + 2 * R * TY;
-  if (threadIdx.x < NH) {
+  for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
+  x0 = (t % p.tiles_x) * TILE;
+  y0 = (t / p.tiles_x) * TILE;
+  S qprev[RPT][4];
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) {
+    const int r = tg + k * NG;
+    form(x0 + tx, y0 + r, r + R, tx + R, qprev[k]);
+  }
+  constexpr int NH_ROW = 2 * R * TILE, NH = 2 * NH_ROW;
+  for (int h = threadIdx.x; h < NH; h += NTP) {
     int row, col;
-    const int h = threadIdx.x;
-    if (h < NH_ROW) {
-      const int r = h / TX;
-      row = (r < R) ? r : TY + r;
-      col = (h % TX) + R;
-    } else {
+    if (h < NH_ROW) {               // rows above / below
+      const int r = h / TILE;
+      row = (r < R) ? r : TILE + r;
+      col = (h % TILE) + R;
+    } else {                        // columns left / right
       const int h2 = h - NH_ROW;
       row = h2 / (2 * R) + R;
       const int c = h2 % (2 * R);
-      col = (c < R) ? c : TX + c;
+      col = (c < R) ? c : TILE + c;
     }
-    vec4 dummy;
-    tile[row][col] = form(x0 + col - R, y0 + row - R, dummy);
+    S dummy[4];
+    form(x0 + col - R, y0 + row - R, row, col, dummy);
   }
   __syncthreads();
 
-  const int x = x0 + tx, y = y0 + ty;
-  double P = 0.0, Y = 0.0, Xn = 0.0;
-  if (x < nx && y < ny) {
-    const size_t idx = (size_t)y * nx + x;
-    const int r = ty + R, c = tx + R;
-    const vec4 C = tile[r][c];
-    double dxu_r, dxu_i, dxd_r, dxd_i, dyu_r, dyu_i, dyd_r, dyd_i;
-    {
-      const vec4 E1 = tile[r][c + 1], W1 = tile[r][c - 1];
-      const vec4 N1 = tile[r + 1][c], S1 = tile[r - 1][c];
-      dxu_r = E1.x - W1.x; dxu_i = E1.y - W1.y; dxd_r = E1.z - W1.z; dxd_i = E1.w - W1.w;
-      dyu_r = N1.x - S1.x; dyu_i = N1.y - S1.y; dyd_r = N1.z - S1.z; dyd_i = N1.w - S1.w;
-      if constexpr (R == 2) {
-        const vec4 E2 = tile[r][c + R], W2 = tile[r][c - R];
-        const vec4 N2 = tile[r + R][c], S2 = tile[r - R][c];
-        dxu_r = fma(8.0, dxu_r, W2.x - E2.x); dxu_i = fma(8.0, dxu_i, W2.y - E2.y);
-        dxd_r = fma(8.0, dxd_r, W2.z - E2.z); dxd_i = fma(8.0, dxd_i, W2.w - E2.w);
-        dyu_r = fma(8.0, dyu_r, S2.x - N2.x); dyu_i = fma(8.0, dyu_i, S2.y - N2.y);
-        dyd_r = fma(8.0, dyd_r, S2.z - N2.z); dyd_i = fma(8.0, dyd_i, S2.w - N2.w);
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) {
+    const int ry = tg + k * NG;
+    const int x = x0 + tx, y = y0 + ry;
+    if (x < nx && y < ny) {
+      const size_t idx = (size_t)y * nx + x;
+      const int r = ry + R, c = tx + R;
+      S C[4], dxv[4], dyv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        C[q] = tile[r][c][q];
+        dxv[q] = tile[r][c + 1][q] - tile[r][c - 1][q];
+        dyv[q] = tile[r + 1][c][q] - tile[r - 1][c][q];
+        if constexpr (R == 2) {
+          dxv[q] = fma(S(8), dxv[q], tile[r][c - 2][q] - tile[r][c + 2][q]);
+          dyv[q] = fma(S(8), dyv[q], tile[r - 2][c][q] - tile[r + 2][c][q]);
+        }
+      }
+      S au, ad;
+      if constexpr (HAS_V) {       // V stored in S (float copy on the mixed path)
+        const S v = static_cast<const S*>(p.V)[idx];
+        au = au_hi + v;
+        ad = ad_hi + v;
+      } else {
+        au = au_hi;
+        ad = ad_hi;
+      }
+      // C = (u.re, u.im, d.re, d.im); dxv/dyv likewise
+      S yv[4];
+      // upper: (mc^2+V-s-sigma) u + c[-i D_x d - D_y d + (A_x - i A_y) d]
+      yv[0] = au * C[0] + kx * dxv[3] - ky * dyv[2] + cAx * C[2] + cAy * C[3];
+      yv[1] = au * C[1] - kx * dxv[2] - ky * dyv[3] + cAx * C[3] - cAy * C[2];
+      // lower: (-mc^2+V-s-sigma) d + c[-i D_x u + D_y u + (A_x + i A_y) u]
+      yv[2] = ad * C[2] + kx * dxv[1] + ky * dyv[0] + cAx * C[0] - cAy * C[1];
+      yv[3] = ad * C[3] - kx * dxv[0] + ky * dyv[1] + cAx * C[1] + cAy * C[0];
+      if constexpr (sizeof(S) == sizeof(float)) {
+        yv[0] = fma(au_lo, C[0], yv[0]);
+        yv[1] = fma(au_lo, C[1], yv[1]);
+        yv[2] = fma(ad_lo, C[2], yv[2]);
+        yv[3] = fma(ad_lo, C[3], yv[3]);
+      }
+      if (i >= 2) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) yv[q] = fma(-eS, qprev[k][q], yv[q]);
+      }
+      if (!p.probe) {
+        if (p.q_out) {
+          T4 o; o.x = C[0]; o.y = C[1]; o.z = C[2]; o.w = C[3];
+          static_cast<T4*>(p.q_out)[idx] = o;
+        }
+        if (p.y_out) {
+          T4 o; o.x = yv[0]; o.y = yv[1]; o.z = yv[2]; o.w = yv[3];
+          static_cast<T4*>(p.y_out)[idx] = o;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        accP = fma(C[q], yv[q], accP);
+        accY = fma(yv[q], yv[q], accY);
+        accX = fma(C[q], C[q], accX);
       }
     }
-    double au = p.mcc - p.shift - sigma, ad = -p.mcc - p.shift - sigma;
-    if (HAS_V) {
-      const double v = p.V[idx];
-      au += v;
-      ad += v;
-    }
-    const double kx = p.kx, ky = p.ky, cAx = p.cAx, cAy = p.cAy;
-    vec4 yv;
-    // upper: (mc^2+V-s-sigma) u + c[-i D_x d - D_y d + (A_x - i A_y) d]
-    yv.x = au * C.x + kx * dxd_i - ky * dyd_r + cAx * C.z + cAy * C.w;
-    yv.y = au * C.y - kx * dxd_r - ky * dyd_i + cAx * C.w - cAy * C.z;
-    // lower: (-mc^2+V-s-sigma) d + c[-i D_x u + D_y u + (A_x + i A_y) u]
-    yv.z = ad * C.z + kx * dxu_i + ky * dyu_r + cAx * C.x - cAy * C.y;
-    yv.w = ad * C.w - kx * dxu_r + ky * dyu_i + cAx * C.y + cAy * C.x;
-    if (i >= 2) {
-      yv.x = fma(-e, qprev.x, yv.x);
-      yv.y = fma(-e, qprev.y, yv.y);
-      yv.z = fma(-e, qprev.z, yv.z);
-      yv.w = fma(-e, qprev.w, yv.w);
-    }
-    if (!p.probe) {
-      if (p.q_out) p.q_out[idx] = C;
-      if (p.y_out) p.y_out[idx] = yv;
-    }
-    P = C.x * yv.x + C.y * yv.y + C.z * yv.z + C.w * yv.w;
-    Y = yv.x * yv.x + yv.y * yv.y + yv.z * yv.z + yv.w * yv.w;
-    Xn = C.x * C.x + C.y * C.y + C.z * C.z + C.w * C.w;
+  }
+  __syncthreads();   // the tile is reused by the next iteration
   }
 
-  // CTA reduction in a fixed order
-  P = warp_sum(P);
-  Y = warp_sum(Y);
-  Xn = warp_sum(Xn);
+  // the next kernel may be scheduled now (it waits for our completion)
+  asm volatile("griddepcontrol.launch_dependents;");
+  // reductions: thread -> warp in S, warp -> CTA in double (fixed order)
+  accP = warp_sum_t(accP);
+  accY = warp_sum_t(accY);
+  accX = warp_sum_t(accX);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) { red[warp][0] = P; red[warp][1] = Y; red[warp][2] = Xn; }
+  if (lane == 0) { red[warp][0] = (double)accP; red[warp][1] = (double)accY; red[warp][2] = (double)accX; }
   __syncthreads();
-  const unsigned ncta = gridDim.x * gridDim.y;
-  const unsigned cta = blockIdx.y * gridDim.x + blockIdx.x;
+  const unsigned ncta = gridDim.x;
+  const unsigned cta = blockIdx.x;
   if (threadIdx.x == 0) {
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
 #pragma unroll
-    for (int w = 0; w < NT / 32; ++w) { s0 += red[w][0]; s1 += red[w][1]; s2 += red[w][2]; }
+    for (int w = 0; w < NTP / 32; ++w) { s0 += red[w][0]; s1 += red[w][1]; s2 += red[w][2]; }
     p.partials[3 * (size_t)cta + 0] = s0;
     p.partials[3 * (size_t)cta + 1] = s1;
     p.partials[3 * (size_t)cta + 2] = s2;
-    __threadfence();
-    const unsigned ticket = atomicAdd((unsigned*)&p.st->counter, 1u);
-    last_cta = (ticket == ncta - 1);
+    // release our partials / acquire everybody else's
+    cuda::atomic_ref<unsigned, cuda::thread_scope_device> ticket(p.st->counter);
+    last_cta = (ticket.fetch_add(1u, cuda::memory_order_acq_rel) == ncta - 1);
   }
   __syncthreads();
-  if (!last_cta) return;
+  if (!last_cta || warp != 0) return;
 
-  // last CTA: sum all partials in a fixed order
-  __threadfence();
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-  for (unsigned b = threadIdx.x; b < ncta; b += NT) {
-    s0 += __ldcg(p.partials + 3 * (size_t)b + 0);
-    s1 += __ldcg(p.partials + 3 * (size_t)b + 1);
-    s2 += __ldcg(p.partials + 3 * (size_t)b + 2);
+  // last CTA, warp 0: sum all partials in a fixed order
+  double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+  for (unsigned b = lane; b < ncta; b += 32) {
+    t0 += __ldcg(p.partials + 3 * (size_t)b + 0);
+    t1 += __ldcg(p.partials + 3 * (size_t)b + 1);
+    t2 += __ldcg(p.partials + 3 * (size_t)b + 2);
   }
-  s0 = warp_sum(s0);
-  s1 = warp_sum(s1);
-  s2 = warp_sum(s2);
-  __syncthreads();
-  if (lane == 0) { red[warp][0] = s0; red[warp][1] = s1; red[warp][2] = s2; }
-  __syncthreads();
-  if (warp == 0) {
-    double t0 = 0.0, t1 = 0.0, t2 = 0.0;
-#pragma unroll
-    for (int w = 0; w < NT / 32; ++w) { t0 += red[w][0]; t1 += red[w][1]; t2 += red[w][2]; }
-    if (lane == 0) st->counter = 0u;
-    finish_pass(p, t0, t1, t2);
-  }
+  t0 = warp_sum(t0);
+  t1 = warp_sum(t1);
+  t2 = warp_sum(t2);
+  if (lane == 0) p.st->counter = 0u;
+  finish_pass(p, t0, t1, t2);
 }
 
 // ---------------------------------------------------------------------------
@@ -399,6 +505,7 @@ __global__ void __launch_bounds__(NT) lanczos_pass(const __grid_constant__ PassP
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) recombine(vec4* psi, const vec4* __restrict__ basis,
                                                  long long n_sites, DevState* st_) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   __shared__ double cr[KMAX + 2], ci[KMAX + 2];
   __shared__ int k_s, err_s;
   volatile DevState* st = st_;
@@ -428,13 +535,59 @@ __global__ void __launch_bounds__(256) recombine(vec4* psi, const vec4* __restri
 }
 
 // ---------------------------------------------------------------------------
+// Mixed path: psi <- C_1 psi + sum_{j>=2} C_j q^_j with psi complex128 and the
+// basis complex64.  C_1 psi is formed in FP64 so that the FP32 rounding of the
+// basis only enters the (small) Krylov corrections.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) recombine_mixed(double4_32a* psi, const float4* __restrict__ basis,
+                                                       long long n_sites, DevState* st_) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  __shared__ double c1r, c1i;
+  __shared__ float cr[KMAX + 2], ci[KMAX + 2];
+  __shared__ int k_s, err_s;
+  volatile DevState* st = st_;
+  if (threadIdx.x == 0) {
+    k_s = st->k_used; err_s = st->error;
+    c1r = st->coef_re[1]; c1i = st->coef_im[1];
+  }
+  if (threadIdx.x <= KMAX) { cr[threadIdx.x] = (float)st->coef_re[threadIdx.x]; ci[threadIdx.x] = (float)st->coef_im[threadIdx.x]; }
+  __syncthreads();
+  if (err_s) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->stopped = 0;
+  const int k = k_s;
+  const double ar = c1r, ai = c1i;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n_sites; s += stride) {
+    float ur = 0.f, ui = 0.f, dr = 0.f, di = 0.f;
+    for (int j = 2; j <= k; ++j) {
+      const float4 b = basis[(size_t)(j - 2) * n_sites + s];
+      const float a = cr[j], bb = ci[j];
+      ur = fmaf(a, b.x, fmaf(-bb, b.y, ur));
+      ui = fmaf(a, b.y, fmaf(bb, b.x, ui));
+      dr = fmaf(a, b.z, fmaf(-bb, b.w, dr));
+      di = fmaf(a, b.w, fmaf(bb, b.z, di));
+    }
+    const double4_32a q = psi[s];
+    double4_32a o;
+    o.x = fma(ar, q.x, fma(-ai, q.y, (double)ur));
+    o.y = fma(ar, q.y, fma(ai, q.x, (double)ui));
+    o.z = fma(ar, q.z, fma(-ai, q.w, (double)dr));
+    o.w = fma(ar, q.w, fma(ai, q.z, (double)di));
+    psi[s] = o;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // test hook: exp(-i T dt) e_1 for a given T with the device routine
 // ---------------------------------------------------------------------------
 __global__ void debug_tridiag_expm(const __grid_constant__ ChebParams cp, int k, const double* alpha1,
                                    const double* beta1, double* out_re, double* out_im) {
   double vr, vi;
-  cheb_expm_e1(cp, k, alpha1, beta1, vr, vi);
   const int lane = threadIdx.x & 31;
+  const double a = lane < k ? alpha1[lane + 1] : 0.0;
+  const double bl = (lane >= 1 && lane < k) ? beta1[lane] : 0.0;
+  const double bh = (lane + 1 < k) ? beta1[lane + 1] : 0.0;
+  cheb_expm_e1(cp, k, a, bl, bh, vr, vi);
   if (lane < k) { out_re[lane] = vr; out_im[lane] = vi; }
 }
 

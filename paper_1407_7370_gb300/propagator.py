@@ -49,14 +49,16 @@ class Propagator:
     """Lanczos propagator for one grid; see include/dirac.h for the semantics."""
 
     def __init__(self, nx: int, ny: int, dx: float, dy: float, mass: float = 1.0,
-                 c: float = 137.036, order: int = 2, boundary: str = "periodic", m_max: int = 20):
+                 c: float = 137.036, order: int = 2, boundary: str = "periodic", m_max: int = 20,
+                 precision: str = "fp64"):
         L = nat.lib()
         self.nx, self.ny = nx, ny
         b = {"periodic": nat.PERIODIC, "dirichlet": nat.DIRICHLET}[boundary]
+        prec = {"fp64": nat.FP64, "mixed": nat.MIXED}[precision]
         self._ctx = ctypes.c_void_p()
         self._stream = _stream_ptr()
         nat.check(L.dirac_create(ctypes.byref(self._ctx), nx, ny, dx, dy, mass, c, order, b,
-                                 nat.FP64, m_max, self._stream))
+                                 prec, m_max, self._stream))
 
     def _sync_stream(self):
         s = _stream_ptr()

@@ -35,9 +35,10 @@ def built():
 
 
 def gpu_run(grid, psi0, dt, m, steps, V=None, A=(0.0, 0.0), order=2, boundary="periodic",
-            shift=0.0, tol=0.0, A_steps=None, info=True):
+            shift=0.0, tol=0.0, A_steps=None, info=True, precision="fp64"):
     from paper_1407_7370_gb300 import Propagator
-    prop = Propagator(grid.nx, grid.ny, grid.dx, grid.dy, order=order, boundary=boundary, m_max=m)
+    prop = Propagator(grid.nx, grid.ny, grid.dx, grid.dy, order=order, boundary=boundary, m_max=m,
+                      precision=precision)
     prop.set_fields(None if V is None else torch.from_numpy(V).cuda(), A=A, shift=shift)
     psi = torch.from_numpy(np.ascontiguousarray(psi0)).cuda()
     inf = prop.steps(psi, steps, dt, m, tol=tol, A=A_steps, info=info)
@@ -254,3 +255,66 @@ def test_laser_packet_1024_full_size():
     exact = free.propagate(oracle_op(g), psi0.copy(), dt, n, pulse=p, t0=t0)
     assert ham.norm(out - exact) <= info.cum_err + 1e-12 * ham.norm(exact)
     assert abs(ham.norm(out) - ham.norm(psi0)) <= 1e-12 * ham.norm(psi0)
+
+
+# ---------------------------------------------------------------------------
+# Mixed path: complex64 basis and FP32 stencil, FP64 scalars and state.
+# Tolerance: relative L2 of psi at most 1e-5 per unit of simulated time
+# against the FP64 oracle, with a floor of 1e-8 per step for short runs (the
+# complex64 rounding of the basis, 6e-8, times the Krylov coefficients beyond
+# the first, at most ~0.1 here).
+# ---------------------------------------------------------------------------
+def mixed_tol(steps, dt):
+    return max(1e-5 * steps * dt, 1e-8 * steps)
+
+
+def test_mixed_free_packet_64_full_run():
+    cfg = wl.FREE_PACKET_64
+    g = cfg["grid"]
+    psi0 = wl.positive_energy_packet(g, p0=cfg["p0"], sigma_x=cfg["sigma_x"])
+    out, info, _ = gpu_run(g, psi0, cfg["dt"], cfg["m"], cfg["steps"], precision="mixed")
+    ref, _ = lz.propagate(oracle_op(g), psi0.copy(), cfg["dt"], cfg["m"], cfg["steps"])
+    assert lz.rel_l2(out, ref) <= 1e-5 * cfg["steps"] * cfg["dt"]
+    assert abs(ham.norm(out) - ham.norm(psi0)) <= 1e-9 * ham.norm(psi0)
+
+
+@pytest.mark.parametrize("nx,ny,order,boundary,hasv,A", CASES[:4] + CASES[5:6])
+def test_mixed_ragged_and_boundary_grids(nx, ny, order, boundary, hasv, A):
+    g = wl.Grid(nx, ny, 0.1, 0.13)
+    psi0 = wl.random_spinor(g, nx * 100 + ny) * 0.1
+    V = wl.random_potential(g, 7, scale=20.0) if hasv else None
+    dt, m, steps = 1e-4, 6, 3
+    b = ham.DIRICHLET if boundary == "dirichlet" else ham.PERIODIC
+    out, info, _ = gpu_run(g, psi0, dt, m, steps, V=V, A=A, order=order, boundary=boundary,
+                           precision="mixed")
+    ref, _ = lz.propagate(oracle_op(g, V=V, A=A, order=order, boundary=b), psi0.copy(), dt, m, steps)
+    # a random (white-noise) field has the full spectral width, so the FP32
+    # Krylov corrections are O(1) here: hold it to FP32 rounding, not 1e-5 t
+    assert lz.rel_l2(out, ref) <= 1e-6 * steps
+
+
+def test_mixed_step_scalars_match_oracle():
+    g = wl.Grid(64, 48, 0.1, 0.1)
+    psi0 = wl.positive_energy_packet(g, p0=(10.0, 5.0))
+    V = wl.smoothed_coulomb(g, 3.0, 0.5)
+    dt, m = 1e-4, 12
+    out, info, _ = gpu_run(g, psi0, dt, m, 1, V=V, A=(4.0, -2.0), precision="mixed")
+    ref, oi = lz.krylov_step(oracle_op(g, V=V, A=(4.0, -2.0)), psi0.copy(), dt, m)
+    assert info.k_used == oi.k_used == m
+    assert abs(info.energy - oi.energy) <= 1e-9 * abs(oi.energy)
+    assert abs(info.norm - oi.norm) <= 1e-7 * oi.norm
+    assert np.allclose(info.alpha[:4], oi.alpha[:4] / dt, rtol=1e-6)
+    assert lz.rel_l2(out, ref) <= mixed_tol(1, dt)
+
+
+@pytest.mark.slow
+def test_mixed_laser_packet_1024_against_closed_form():
+    from paper_1407_7370_gb300.propagator import pulse_schedule
+    cfg = wl.LASER_PACKET_1024
+    g, p = cfg["grid"], cfg["pulse"]
+    psi0 = wl.positive_energy_packet(g, p0=cfg["p0"], sigma_x=cfg["sigma_x"])
+    dt, m, t0, n = cfg["dt"], cfg["m"], 0.3, 100
+    An = pulse_schedule(t0, dt, n, p.a0, p.omega, p.duration)
+    out, info, _ = gpu_run(g, psi0, dt, m, n, A_steps=An, precision="mixed")
+    exact = free.propagate(oracle_op(g), psi0.copy(), dt, n, pulse=p, t0=t0)
+    assert lz.rel_l2(out, exact) <= mixed_tol(n, dt)
