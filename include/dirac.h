@@ -61,6 +61,8 @@ typedef struct {
     double energy;     /* <psi|H|psi>/<psi|psi> before the step (hartree) */
     double alpha[DIRAC_KRYLOV_MAX];  /* T diagonal, of H - energy_shift (hartree) */
     double beta[DIRAC_KRYLOV_MAX];   /* beta[i] couples i, i+1; beta[k-1] = beta_k */
+    double kappa_max;  /* largest ||y^||^2 / (||y^||^2 - P^2/X) of a pass since create:
+                          the cancellation in the fused beta estimate */
 } dirac_step_info;
 
 /*
@@ -170,6 +172,53 @@ const char* dirac_status_string(dirac_status s);
 
 /* Message of the last error raised on the calling thread ("" if none). */
 const char* dirac_last_error(void);
+
+/*
+ * Batches: many independent propagations advanced together (one launch per
+ * Lanczos iteration covers every problem of the batch, so the per-launch
+ * costs are shared).  All problems share mass, c, stencil order, boundary,
+ * precision, m_max, dt, m and tol; each has its own grid (nx[b] x ny[b],
+ * spacings dx[b], dy[b]), state, potential, shift and vector potential.
+ * The semantics per problem are those of the single-problem calls above.
+ * Errors as dirac_create / dirac_lanczos_steps.
+ */
+typedef struct dirac_batch dirac_batch;
+
+dirac_status dirac_batch_create(dirac_batch** out, int n_problems, const int* nx, const int* ny,
+                                const double* dx, const double* dy, double mass, double c,
+                                int stencil_order, int boundary, int precision, int m_max,
+                                void* cuda_stream);
+void dirac_batch_destroy(dirac_batch* batch);
+
+/* As dirac_set_fields, for problem `problem` (0-based). */
+dirac_status dirac_batch_set_fields(dirac_batch* batch, int problem, const double* V_dev,
+                                    double A_x, double A_y, double energy_shift);
+
+/*
+ * Launch shape of the Lanczos passes: tile height 32 or 16 sites (mixed
+ * precision only; FP64 always uses 32) and a cap on resident CTAs per SM
+ * (0: no cap).  Used by the autotuner; results do not depend on it beyond
+ * the order of floating-point sums.
+ */
+dirac_status dirac_batch_set_launch_shape(dirac_batch* batch, int tile_height, int ctas_per_sm);
+
+/*
+ * nsteps steps of every problem, in place.  psi_dev: n_problems device
+ * pointers (complex128 [ny[b]][nx[b]][2], 32-byte aligned).  A_xy_host:
+ * host array [nsteps][n_problems][2] of per-step vector potentials, or NULL
+ * to keep each problem's current one.  info: n_problems entries or NULL
+ * (synchronises when given).
+ */
+dirac_status dirac_batch_steps(dirac_batch* batch, void* const* psi_dev, int nsteps, double dt,
+                               int m, double tol, const double* A_xy_host, dirac_step_info* info);
+
+/* Wait for the batch's stream and fill info (n_problems entries, may be NULL). */
+dirac_status dirac_batch_sync(dirac_batch* batch, dirac_step_info* info);
+
+/* dirac_profile_enable / dirac_profile_read / dirac_kernel_launches for a batch. */
+dirac_status dirac_batch_profile_enable(dirac_batch* batch, int enable);
+dirac_status dirac_batch_profile_read(dirac_batch* batch, double* ms, long long* launches);
+long long dirac_batch_kernel_launches(const dirac_batch* batch);
 
 /*
  * Allocation-free single step.  The paper has no counterpart: this entry

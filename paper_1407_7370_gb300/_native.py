@@ -26,7 +26,8 @@ class StepInfoC(ctypes.Structure):
     _fields_ = [("k_used", ctypes.c_int), ("breakdown", ctypes.c_int),
                 ("err_est", ctypes.c_double), ("cum_err", ctypes.c_double),
                 ("norm", ctypes.c_double), ("energy", ctypes.c_double),
-                ("alpha", ctypes.c_double * KRYLOV_MAX), ("beta", ctypes.c_double * KRYLOV_MAX)]
+                ("alpha", ctypes.c_double * KRYLOV_MAX), ("beta", ctypes.c_double * KRYLOV_MAX),
+                ("kappa_max", ctypes.c_double)]
 
 
 class ProblemC(ctypes.Structure):
@@ -80,6 +81,16 @@ def lib():
         "dirac_lanczos_step_noalloc": (i, [ctypes.POINTER(ProblemC), vp, d, i, d, vp,
                                            ctypes.POINTER(StepInfoC)]),
         "dirac_noalloc_scratch_bytes": (ctypes.c_size_t, []),
+        "dirac_batch_create": (i, [ctypes.POINTER(vp), i, ctypes.POINTER(i), ctypes.POINTER(i), dp, dp,
+                                   d, d, i, i, i, i, vp]),
+        "dirac_batch_destroy": (None, [vp]),
+        "dirac_batch_set_fields": (i, [vp, i, vp, d, d, d]),
+        "dirac_batch_set_launch_shape": (i, [vp, i, i]),
+        "dirac_batch_steps": (i, [vp, ctypes.POINTER(vp), i, d, i, d, dp, ctypes.POINTER(StepInfoC)]),
+        "dirac_batch_sync": (i, [vp, ctypes.POINTER(StepInfoC)]),
+        "dirac_batch_profile_enable": (i, [vp, i]),
+        "dirac_batch_profile_read": (i, [vp, dp, ctypes.POINTER(ctypes.c_longlong)]),
+        "dirac_batch_kernel_launches": (ctypes.c_longlong, [vp]),
         "dirac_profile_read": (i, [vp, dp, ctypes.POINTER(ctypes.c_longlong)]),
     }
     for name, (res, args) in sig.items():

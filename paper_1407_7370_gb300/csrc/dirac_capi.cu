@@ -1,5 +1,5 @@
-// dirac_capi.cu -- host side of the GB300 Dirac Lanczos propagator: context,
-// workspace, launch sequencing and the C ABI declared in include/dirac.h.
+// dirac_capi.cu -- host side of the GB300 Dirac Lanczos propagator: problem
+// tables, workspace, launch sequencing and the C ABI of include/dirac.h.
 #include "dirac.h"
 #include "dirac_kernels.cuh"
 
@@ -36,74 +36,51 @@ dirac_status fail(dirac_status s, const char* fmt, ...) {
     if (e_ != cudaSuccess) return fail(DIRAC_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
 
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+bool aligned32(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 31u) == 0; }
+size_t site_bytes(int precision) { return precision == DIRAC_FP64 ? sizeof(double4_32a) : sizeof(float4); }
+
+// ---------------------------------------------------------------------------
+// small exponential: Jacobi-Anger coefficients on an a-priori interval
+// ---------------------------------------------------------------------------
+
 // Bessel functions J_0..J_{n-1}(x), x > 0, by Miller's backward recurrence
 // J_{k-1} = (2k/x) J_k - J_{k+1} started far above n and normalised with
-// J_0 + 2 sum_{k>=1} J_{2k} = 1.
-std::vector<double> bessel_j(int n, double x) {
+// J_0 + 2 sum_{k>=1} J_{2k} = 1.  Stack storage only.
+bool bessel_j(int n, double x, double* out) {
+  constexpr int NJ = 512;
+  double j[NJ + 2];
   const int start = 2 * ((std::max(n, (int)x) + 40 + (int)std::sqrt(40.0 * std::max(x, 1.0))) / 2);
-  std::vector<double> j(start + 2, 0.0);
-  j[start + 1] = 0.0;
+  if (start > NJ) return false;
+  for (int k = 0; k <= start + 1; ++k) j[k] = 0.0;
   j[start] = 1e-300;
   for (int k = start; k >= 1; --k) {
     j[k - 1] = (2.0 * k / x) * j[k] - j[k + 1];
-    if (std::fabs(j[k - 1]) > 1e250) {      // rescale to stay in range
+    if (std::fabs(j[k - 1]) > 1e250)      // rescale to stay in range
       for (int t = k - 1; t <= start; ++t) j[t] *= 1e-250;
-    }
   }
   double norm = j[0];
   for (int k = 2; k <= start; k += 2) norm += 2.0 * j[k];
-  std::vector<double> out(n);
   for (int k = 0; k < n; ++k) out[k] = j[k] / norm;
-  return out;
+  return true;
 }
-
-}  // namespace
-
-struct dirac_ctx {
-  int nx = 0, ny = 0, order = 2, boundary = DIRAC_PERIODIC, precision = DIRAC_FP64, m_max = 1;
-  double dx = 0, dy = 0, mass = 1, c = 137.036;
-  cudaStream_t stream = nullptr;
-  long long n_sites = 0;
-  void* basis = nullptr;          // q^_2 .. q^_m (complex128, or complex64 when mixed)
-  void* ybuf[2] = {nullptr, nullptr};
-  vec4* psi_own = nullptr;        // staging for the host-buffer call
-  void* V = nullptr;              // double, or float when mixed
-  bool has_v = false;
-  double vmin = 0, vmax = 0;
-  double ax = 0, ay = 0, shift = 0;
-  bool fields_set = false;
-  bool need_probe = true;
-  DevState* st = nullptr;
-  DevState* st_host = nullptr;    // pinned
-  double* partials = nullptr;
-  dim3 grid;
-  long long launches = 0;
-  int n_sm = 0;
-  // per-kernel CUDA-event timing (dirac_profile_*)
-  bool profiling = false;
-  std::vector<cudaEvent_t> ev_pool;
-  std::vector<int> ev_kind;
-  size_t ev_used = 0;
-};
-
-namespace {
 
 // Rigorous interval [c0 - half, c0 + half] containing the spectrum of H - s:
 // H = H0(A) + V with spec(H0(A)) = {+-E_k}, E_k <= sqrt(m^2c^4 + c^2 (P_x+|A_x|)^2
 // + c^2 (P_y+|A_y|)^2), P = max |stencil momentum| (1/h for order 2, for order
 // 4 the maximum of (8 sin t - sin 2t)/(6h)), and V_min <= V <= V_max.
-void spectral_interval(const dirac_ctx* c, double& c0, double& half) {
+void spectral_interval(int order, double dx, double dy, double mass, double c, double ax_max,
+                       double ay_max, double vmin, double vmax, double shift, double& c0,
+                       double& half) {
   double pf = 1.0;
-  if (c->order == 4) {
+  if (order == 4) {
     const double cs = 1.0 - std::sqrt(6.0) / 2.0;    // cos t at the maximum
-    const double sn = std::sqrt(1.0 - cs * cs);
-    pf = sn * (4.0 - cs) / 3.0;
+    pf = std::sqrt(1.0 - cs * cs) * (4.0 - cs) / 3.0;
   }
-  const double px = pf / c->dx + std::fabs(c->ax), py = pf / c->dy + std::fabs(c->ay);
-  const double mc2 = c->mass * c->c * c->c;
-  const double emax = std::sqrt(mc2 * mc2 + c->c * c->c * (px * px + py * py));
-  const double vmin = c->has_v ? c->vmin : 0.0, vmax = c->has_v ? c->vmax : 0.0;
-  c0 = 0.5 * (vmin + vmax) - c->shift;
+  const double px = pf / dx + ax_max, py = pf / dy + ay_max;
+  const double mc2 = mass * c * c;
+  const double emax = std::sqrt(mc2 * mc2 + c * c * (px * px + py * py));
+  c0 = 0.5 * (vmin + vmax) - shift;
   half = (emax + 0.5 * (vmax - vmin)) * (1.0 + 1e-8) + 1e-12;
 }
 
@@ -111,7 +88,8 @@ dirac_status make_cheb(double c0, double half, double dt, double shift, ChebPara
   const double R = half * dt;
   if (!(R > 0.0) || R > 90.0)
     return fail(DIRAC_EINVAL, "dt * ||H|| = %.3g outside (0, 90]: take smaller steps", R);
-  std::vector<double> J = bessel_j(CHEB_MAX, R);
+  double J[CHEB_MAX];
+  if (!bessel_j(CHEB_MAX, R, J)) return fail(DIRAC_EINVAL, "dt too large");
   int n = 2;
   for (int k = 0; k < CHEB_MAX; ++k)
     if (std::fabs(J[k]) > 1e-18 || k <= (int)R + 1) n = k + 1;
@@ -134,10 +112,11 @@ dirac_status make_cheb(double c0, double half, double dt, double shift, ChebPara
   return DIRAC_OK;
 }
 
-// Launch with programmatic stream serialisation: the kernel may be scheduled
-// while the previous kernel in the stream finishes; it waits for it (and sees
-// its writes) at its griddepcontrol.wait.
-// DIRAC_NO_PDL=1 in the environment turns the overlap off (debugging aid).
+// ---------------------------------------------------------------------------
+// launches
+// ---------------------------------------------------------------------------
+
+// DIRAC_NO_PDL=1 in the environment turns the launch overlap off (debugging aid).
 bool pdl_enabled() {
   static const bool on = [] {
     const char* v = std::getenv("DIRAC_NO_PDL");
@@ -146,6 +125,9 @@ bool pdl_enabled() {
   return on;
 }
 
+// Launch with programmatic stream serialisation: the kernel may be scheduled
+// while the previous kernel in the stream finishes; it waits for it (and sees
+// its writes) at its griddepcontrol.wait.
 template <class... KArgs, class... Args>
 cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream_t s, Args&&... args) {
   cudaLaunchConfig_t cfg = {};
@@ -161,177 +143,60 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream
   return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
-// Persistent launch: as many CTAs as fit on the GPU at once (never more than
-// there are tiles); each CTA walks the tiles with a grid stride.
-template <class S, int R, bool D, bool V, bool Q64>
-cudaError_t launch_pass_t(const PassParams& p, int n_sm, cudaStream_t s) {
+struct LaunchShape {
+  int n_sm;          // SMs of the device
+  int th;            // tile height (32 or 16; FP64 always 32)
+  int cta_cap;       // 0: as many CTAs per SM as fit; else at most this many
+};
+
+// Persistent launch: at most (resident CTAs) CTAs, each taking an equal
+// contiguous chunk of the tile list.
+template <class S, int R, int TH, bool D, bool V>
+cudaError_t launch_pass_t(LaunchParams p, const LaunchShape& ls, cudaStream_t s) {
   static int occ = 0;
+  constexpr int NT = 32 * (TH / RPT);
   if (occ == 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lanczos_pass<S, R, D, V, Q64>, NTP, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lanczos_pass<S, R, TH, D, V>, NT, 0);
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
   }
-  // FP32 (memory-bound): equal work per CTA, T = ceil(tiles / resident CTAs)
-  // tiles each; FP64 (FP64-pipe-bound): fill every slot to hide latency
-  const int slots = std::max(1, n_sm * occ);
-  const int per = (p.ntiles + slots - 1) / slots;
-  const int grid = sizeof(S) == sizeof(float) ? std::max(1, (p.ntiles + per - 1) / per)
-                                              : std::max(1, std::min(p.ntiles, slots));
-  return launch_pdl(lanczos_pass<S, R, D, V, Q64>, grid, NTP, s, p);
+  const int per_sm = ls.cta_cap > 0 ? std::min(occ, ls.cta_cap) : occ;
+  const int slots = std::max(1, ls.n_sm * per_sm);
+  p.tiles_per_cta = (p.total_tiles + slots - 1) / slots;
+  const int grid = std::max(1, (p.total_tiles + p.tiles_per_cta - 1) / p.tiles_per_cta);
+  return launch_pdl(lanczos_pass<S, R, TH, D, V>, grid, NT, s, p);
 }
 
-template <class S, bool Q64>
-cudaError_t launch_pass_s(const dirac_ctx* c, const PassParams& p) {
-  const bool d = c->boundary == DIRAC_DIRICHLET, v = c->has_v;
-  if (c->order == 2) {
-    if (d) return v ? launch_pass_t<S, 1, true, true, Q64>(p, c->n_sm, c->stream) : launch_pass_t<S, 1, true, false, Q64>(p, c->n_sm, c->stream);
-    return v ? launch_pass_t<S, 1, false, true, Q64>(p, c->n_sm, c->stream) : launch_pass_t<S, 1, false, false, Q64>(p, c->n_sm, c->stream);
+template <class S, int TH>
+cudaError_t launch_pass_s(int order, bool diri, bool hasv, const LaunchParams& p, const LaunchShape& ls,
+                          cudaStream_t s) {
+  if (order == 2) {
+    if (diri) return hasv ? launch_pass_t<S, 1, TH, true, true>(p, ls, s) : launch_pass_t<S, 1, TH, true, false>(p, ls, s);
+    return hasv ? launch_pass_t<S, 1, TH, false, true>(p, ls, s) : launch_pass_t<S, 1, TH, false, false>(p, ls, s);
   }
-  if (d) return v ? launch_pass_t<S, 2, true, true, Q64>(p, c->n_sm, c->stream) : launch_pass_t<S, 2, true, false, Q64>(p, c->n_sm, c->stream);
-  return v ? launch_pass_t<S, 2, false, true, Q64>(p, c->n_sm, c->stream) : launch_pass_t<S, 2, false, false, Q64>(p, c->n_sm, c->stream);
+  if (diri) return hasv ? launch_pass_t<S, 2, TH, true, true>(p, ls, s) : launch_pass_t<S, 2, TH, true, false>(p, ls, s);
+  return hasv ? launch_pass_t<S, 2, TH, false, true>(p, ls, s) : launch_pass_t<S, 2, TH, false, false>(p, ls, s);
 }
 
-// FP64 path: everything complex128.  Mixed path: passes 1 and 2 read the
-// complex128 state as q^_1, later passes read complex64 basis vectors.
-cudaError_t launch_pass(const dirac_ctx* c, const PassParams& p) {
-  if (c->precision == DIRAC_FP64) return launch_pass_s<double, true>(c, p);
-  if (p.pass <= 2) return launch_pass_s<float, true>(c, p);
-  return launch_pass_s<float, false>(c, p);
+// FP64 path: everything complex128.  Mixed path: complex64 basis (passes 1
+// and 2 read the complex128 state as q^_1; the kernel picks per problem).
+cudaError_t launch_pass(int precision, int order, bool diri, bool hasv, const LaunchParams& p,
+                        const LaunchShape& ls, cudaStream_t s) {
+  if (precision == DIRAC_FP64) return launch_pass_s<double, 32>(order, diri, hasv, p, ls, s);
+  if (ls.th == 16) return launch_pass_s<float, 16>(order, diri, hasv, p, ls, s);
+  return launch_pass_s<float, 32>(order, diri, hasv, p, ls, s);
 }
 
-size_t site_bytes(int precision) { return precision == DIRAC_FP64 ? sizeof(double4_32a) : sizeof(float4); }
+// Re-runs of a pass allowed per step (each costs one spare launch, which
+// exits at once when unused) and the cancellation ratio that triggers one:
+// with y^ stored to unit roundoff u, s2 = ||y^||^2 - P^2/X keeps about
+// u * kappa relative accuracy.
+int redo_budget(int precision, int m) { return precision == DIRAC_FP64 ? 2 : 2 + m / 5; }
+double kappa_redo(int precision) { return precision == DIRAC_FP64 ? 1e12 : 1e6; }
 
-bool aligned32(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 31u) == 0; }
-
-enum { KIND_PASS = 0, KIND_RECOMBINE = 1, KIND_END = -1 };
-
-// with profiling on, an event is recorded before every launch and after each step
-cudaError_t mark(dirac_ctx* c, int kind) {
-  if (!c->profiling) return cudaSuccess;
-  if (c->ev_used == c->ev_pool.size()) {
-    cudaEvent_t ev;
-    cudaError_t e = cudaEventCreate(&ev);
-    if (e != cudaSuccess) return e;
-    c->ev_pool.push_back(ev);
-    c->ev_kind.push_back(kind);
-  }
-  c->ev_kind[c->ev_used] = kind;
-  return cudaEventRecord(c->ev_pool[c->ev_used++], c->stream);
-}
-
-// enqueue one full time step on psi (device)
-dirac_status enqueue_step(dirac_ctx* c, vec4* psi, double dt, int m, double tol) {
-  PassParams p;
-  std::memset(&p, 0, sizeof(p));
-  double c0, half;
-  spectral_interval(c, c0, half);
-  dirac_status s = make_cheb(c0, half, dt, c->shift, p.cheb);
-  if (s != DIRAC_OK) return s;
-  const double kfac = (c->order == 2) ? 2.0 : 12.0;
-  p.psi = psi;
-  p.V = c->has_v ? c->V : nullptr;
-  p.st = c->st;
-  p.partials = c->partials;
-  p.nx = c->nx;
-  p.ny = c->ny;
-  p.tiles_x = c->grid.x;
-  p.ntiles = c->grid.x * c->grid.y;
-  p.m = m;
-  p.kx = c->c / (kfac * c->dx);
-  p.ky = c->c / (kfac * c->dy);
-  p.mcc = c->mass * c->c * c->c;
-  p.cAx = c->c * c->ax;   // electron: p - qA = p + A
-  p.cAy = c->c * c->ay;
-  p.shift = c->shift;
-  p.dt = dt;
-  p.tol = tol;
-  p.kxf = (float)p.kx; p.kyf = (float)p.ky; p.cAxf = (float)p.cAx; p.cAyf = (float)p.cAy;
-  p.probe_coef = make_coef(1.0, 0.0, 0.0, p.mcc - p.shift, -p.mcc - p.shift);
-  const long long n = c->n_sites;
-  const size_t sb = site_bytes(c->precision);
-  char* basis = static_cast<char*>(c->basis);
-  if (c->need_probe) {
-    p.pass = 1;
-    p.probe = 1;
-    CUDA_TRY(mark(c, KIND_PASS));
-    CUDA_TRY(launch_pass(c, p));
-    ++c->launches;
-    p.probe = 0;
-    c->need_probe = false;
-  }
-  for (int i = 1; i <= m; ++i) {
-    p.pass = i;
-    p.y_prev = (i >= 2) ? c->ybuf[(i - 1) & 1] : nullptr;
-    p.q_prev = (i == 2) ? (const void*)psi : (i >= 3 ? (const void*)(basis + (size_t)(i - 3) * n * sb) : nullptr);
-    p.q_out = (i >= 2) ? (void*)(basis + (size_t)(i - 2) * n * sb) : nullptr;
-    p.y_out = (i < m) ? c->ybuf[i & 1] : nullptr;
-    CUDA_TRY(mark(c, KIND_PASS));
-    CUDA_TRY(launch_pass(c, p));
-    ++c->launches;
-  }
-  const int rb = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, (long long)c->n_sm * 8));
-  CUDA_TRY(mark(c, KIND_RECOMBINE));
-  if (c->precision == DIRAC_FP64)
-    CUDA_TRY(launch_pdl(recombine, rb, 256, c->stream, psi, static_cast<const vec4*>(c->basis), n, c->st));
-  else
-    CUDA_TRY(launch_pdl(recombine_mixed, rb, 256, c->stream, psi, static_cast<const float4*>(c->basis), n, c->st));
-  ++c->launches;
-  CUDA_TRY(mark(c, KIND_END));
-  return DIRAC_OK;
-}
-
-dirac_status read_state(dirac_ctx* c, dirac_step_info* info) {
-  CUDA_TRY(cudaMemcpyAsync(c->st_host, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
-  CUDA_TRY(cudaStreamSynchronize(c->stream));
-  const DevState& h = *c->st_host;
-  if (h.error) {
-    const int zero[2] = {0, 0};
-    CUDA_TRY(cudaMemcpyAsync(&c->st->stopped, &zero[0], sizeof(int), cudaMemcpyHostToDevice, c->stream));
-    CUDA_TRY(cudaMemcpyAsync(&c->st->error, &zero[1], sizeof(int), cudaMemcpyHostToDevice, c->stream));
-    CUDA_TRY(cudaStreamSynchronize(c->stream));
-    c->need_probe = true;
-    return fail(DIRAC_ENONFINITE, "non-finite value in a Lanczos reduction; psi left unchanged");
-  }
-  if (info) {
-    std::memset(info, 0, sizeof(*info));
-    info->k_used = h.k_used;
-    info->breakdown = h.breakdown;
-    info->err_est = h.err_est;
-    info->cum_err = h.cum_err;
-    info->norm = h.psi_norm;
-    info->energy = h.energy;
-    for (int j = 0; j < h.k_used && j < DIRAC_KRYLOV_MAX; ++j) {
-      info->alpha[j] = h.alpha[j + 1];
-      info->beta[j] = h.beta[j + 1];
-    }
-  }
-  return DIRAC_OK;
-}
-
-dirac_status check_step_args(dirac_ctx* c, const void* psi, double dt, int m, double tol, bool device) {
-  if (!c) return fail(DIRAC_EINVAL, "null context");
-  if (!c->fields_set) return fail(DIRAC_ESTATE, "dirac_set_fields must be called before stepping");
-  if (!psi) return fail(DIRAC_EINVAL, "null psi");
-  if (device && !aligned32(psi)) return fail(DIRAC_EINVAL, "psi must be 32-byte aligned");
-  if (m < 1 || m > c->m_max) return fail(DIRAC_EINVAL, "m = %d outside 1..m_max = %d", m, c->m_max);
-  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(DIRAC_EINVAL, "dt must be finite and > 0");
-  if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(DIRAC_EINVAL, "tol must be finite and >= 0");
-  return DIRAC_OK;
-}
-
-dirac_status run_steps(dirac_ctx* c, vec4* psi, int nsteps, double dt, int m, double tol,
-                       const double* a_xy) {
-  for (int n = 0; n < nsteps; ++n) {
-    if (a_xy) {
-      if (!std::isfinite(a_xy[2 * n]) || !std::isfinite(a_xy[2 * n + 1]))
-        return fail(DIRAC_EINVAL, "non-finite vector potential at step %d", n);
-      c->ax = a_xy[2 * n];
-      c->ay = a_xy[2 * n + 1];
-    }
-    dirac_status s = enqueue_step(c, psi, dt, m, tol);
-    if (s != DIRAC_OK) return s;
-  }
-  return DIRAC_OK;
+cudaError_t launch_recombine(int precision, const RecombParams& rp, int grid, cudaStream_t s) {
+  if (precision == DIRAC_FP64) return launch_pdl(recombine<false>, grid, 256, s, rp);
+  return launch_pdl(recombine<true>, grid, 256, s, rp);
 }
 
 __global__ void to_float_kernel(const double* in, float* out, long long n) {
@@ -342,12 +207,14 @@ __global__ void to_float_kernel(const double* in, float* out, long long n) {
 __global__ void minmax_kernel(const double* v, long long n, double* out) {
   __shared__ double smin[256], smax[256];
   double lo = 1e308, hi = -1e308;
+  bool bad = false;
   for (long long i = threadIdx.x; i < n; i += blockDim.x) {
     const double x = v[i];
     lo = fmin(lo, x);
     hi = fmax(hi, x);
-    if (!isfinite(x)) { lo = -INFINITY; hi = INFINITY; }
+    if (!isfinite(x)) bad = true;
   }
+  if (bad) { lo = -INFINITY; hi = INFINITY; }
   smin[threadIdx.x] = lo;
   smax[threadIdx.x] = hi;
   __syncthreads();
@@ -361,7 +228,438 @@ __global__ void minmax_kernel(const double* v, long long n, double* out) {
   if (threadIdx.x == 0) { out[0] = smin[0]; out[1] = smax[0]; }
 }
 
+// ---------------------------------------------------------------------------
+// Engine: N independent problems sharing precision, stencil, boundary, m_max
+// ---------------------------------------------------------------------------
+enum { KIND_PASS = 0, KIND_RECOMBINE = 1, KIND_END = -1 };
+
+struct HostProblem {
+  int nx = 0, ny = 0;
+  double dx = 0, dy = 0;
+  long long n = 0;
+  int tiles_x = 0, ntiles = 0, tile_begin = 0;
+  int rblk_begin = 0, rblk_count = 0;
+  size_t slot_off = 0;             // first partial slot (3 doubles each)
+  void* basis = nullptr;
+  void* ybuf[2] = {nullptr, nullptr};
+  void* V = nullptr;               // double (FP64) or float (mixed) copy
+  bool has_v = false;
+  double vmin = 0, vmax = 0;
+  double ax = 0, ay = 0, shift = 0;
+  bool fields_set = false;
+};
+
+struct Engine {
+  int order = 2, boundary = DIRAC_PERIODIC, precision = DIRAC_FP64, m_max = 1;
+  double mass = 1, c = 137.036;
+  cudaStream_t stream = nullptr;
+  LaunchShape shape{0, 32, 0};
+  std::vector<HostProblem> P;
+  int total_tiles = 0, rgrid = 0;
+  void* vec_mem = nullptr;         // all basis / y^ fields
+  DevState* d_st = nullptr;        // nprob states
+  DevState* h_st = nullptr;        // pinned mirror for read-back
+  double* d_partials = nullptr;
+  int* d_blk_prob = nullptr;
+  int* d_step = nullptr;
+  // per-call tables: [Problem x nprob][ChebParams x nprob][FieldStep x nfield]
+  void* d_tab = nullptr;
+  void* h_tab = nullptr;           // pinned staging
+  size_t tab_cap = 0;
+  cudaEvent_t tab_ev = nullptr;    // last upload of the staging buffer
+  bool tab_ev_live = false;
+  bool need_probe = true;
+  long long launches = 0;
+  vec4* psi_own = nullptr;         // staging for the host-buffer call
+  // per-kernel CUDA-event timing
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<int> ev_kind;
+  size_t ev_used = 0;
+
+  int nprob() const { return (int)P.size(); }
+  cudaError_t mark(int kind);
+  dirac_status init(int n, const int* nx, const int* ny, const double* dx, const double* dy, double mass_,
+                    double c_, int order_, int boundary_, int precision_, int m_max_, void* stream_);
+  void release();
+  dirac_status set_fields(int b, const double* V_dev, double ax, double ay, double shift);
+  dirac_status run(vec4* const* psi, int nsteps, double dt, int m, double tol, const double* a_xy);
+  dirac_status read_state(dirac_step_info* info);
+  dirac_status set_stream(cudaStream_t s);
+};
+
+cudaError_t Engine::mark(int kind) {
+  if (!profiling) return cudaSuccess;
+  if (ev_used == ev_pool.size()) {
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreate(&ev);
+    if (e != cudaSuccess) return e;
+    ev_pool.push_back(ev);
+    ev_kind.push_back(kind);
+  }
+  ev_kind[ev_used] = kind;
+  return cudaEventRecord(ev_pool[ev_used++], stream);
+}
+
+dirac_status check_common(double mass, double c, int order, int boundary, int precision, int m_max) {
+  if (!(c > 0) || !std::isfinite(c)) return fail(DIRAC_EINVAL, "c must be finite and > 0");
+  if (!(mass >= 0) || !std::isfinite(mass)) return fail(DIRAC_EINVAL, "mass must be finite and >= 0");
+  if (order != 2 && order != 4) return fail(DIRAC_EINVAL, "stencil_order must be 2 or 4");
+  if (boundary != DIRAC_PERIODIC && boundary != DIRAC_DIRICHLET) return fail(DIRAC_EINVAL, "bad boundary");
+  if (precision != DIRAC_FP64 && precision != DIRAC_MIXED)
+    return fail(DIRAC_EINVAL, "precision must be DIRAC_FP64 or DIRAC_MIXED");
+  if (m_max < 1 || m_max > DIRAC_KRYLOV_MAX) return fail(DIRAC_EINVAL, "m_max must be 1..%d", DIRAC_KRYLOV_MAX);
+  return DIRAC_OK;
+}
+
+dirac_status check_grid(int nx, int ny, double dx, double dy) {
+  if (nx < 1 || ny < 1) return fail(DIRAC_EINVAL, "grid %d x %d must be at least 1 x 1", nx, ny);
+  if ((long long)nx * ny > (1LL << 31)) return fail(DIRAC_EINVAL, "grid too large");
+  if (!(dx > 0) || !(dy > 0) || !std::isfinite(dx) || !std::isfinite(dy))
+    return fail(DIRAC_EINVAL, "dx, dy must be finite and > 0");
+  return DIRAC_OK;
+}
+
+// tiles of a problem at tile height th
+int tiles_of(int nx, int ny, int th) { return ((nx + TILE_W - 1) / TILE_W) * ((ny + th - 1) / th); }
+
+dirac_status Engine::init(int n, const int* nx, const int* ny, const double* dx, const double* dy,
+                          double mass_, double c_, int order_, int boundary_, int precision_, int m_max_,
+                          void* stream_) {
+  order = order_; boundary = boundary_; precision = precision_; m_max = m_max_;
+  mass = mass_; c = c_; stream = (cudaStream_t)stream_;
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&shape.n_sm, cudaDevAttrMultiProcessorCount, dev));
+  shape.th = 16;   // mixed path default (FP64 always uses 32-row tiles)
+  P.resize(n);
+  long long sites = 0;
+  size_t slots = 0;
+  for (int b = 0; b < n; ++b) {
+    HostProblem& q = P[b];
+    q.nx = nx[b]; q.ny = ny[b]; q.dx = dx[b]; q.dy = dy[b];
+    q.n = (long long)q.nx * q.ny;
+    q.tiles_x = (q.nx + TILE_W - 1) / TILE_W;
+    q.slot_off = slots;
+    slots += (size_t)tiles_of(q.nx, q.ny, 16);   // at least one tile per slot
+    sites += q.n;
+  }
+  // workspace: (m_max - 1) basis fields + 2 y^ fields per problem, one block
+  const size_t sb = site_bytes(precision);
+  const int nbasis = std::max(1, m_max - 1);
+  size_t vec_bytes = 0;
+  for (const HostProblem& q : P) vec_bytes += (size_t)(nbasis + 2) * align256((size_t)q.n * sb);
+  cudaError_t e = cudaMalloc(&vec_mem, vec_bytes);
+  if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? DIRAC_ENOMEM : DIRAC_ECUDA,
+                                    "workspace (%zu bytes): %s", vec_bytes, cudaGetErrorString(e));
+  char* p = static_cast<char*>(vec_mem);
+  for (HostProblem& q : P) {
+    const size_t f = align256((size_t)q.n * sb);
+    q.basis = p; p += (size_t)nbasis * f;
+    q.ybuf[0] = p; p += f;
+    q.ybuf[1] = p; p += f;
+  }
+  CUDA_TRY(cudaMalloc(&d_partials, 3 * sizeof(double) * std::max<size_t>(slots, 1)));
+  CUDA_TRY(cudaMalloc(&d_st, sizeof(DevState) * n));
+  CUDA_TRY(cudaMallocHost(&h_st, sizeof(DevState) * n));
+  CUDA_TRY(cudaMalloc(&d_step, sizeof(int)));
+  CUDA_TRY(cudaMemsetAsync(d_st, 0, sizeof(DevState) * n, stream));
+  CUDA_TRY(cudaEventCreateWithFlags(&tab_ev, cudaEventDisableTiming));
+  // recombination blocks in proportion to the problem sizes
+  const long long rmax = std::max<long long>(n, (long long)shape.n_sm * 8);
+  std::vector<int> blk;
+  for (int b = 0; b < n; ++b) {
+    HostProblem& q = P[b];
+    long long want = (long long)((double)rmax * (double)q.n / (double)sites + 0.5);
+    want = std::max<long long>(1, std::min<long long>(want, (q.n + 255) / 256));
+    q.rblk_begin = (int)blk.size();
+    q.rblk_count = (int)want;
+    for (long long k = 0; k < want; ++k) blk.push_back(b);
+  }
+  rgrid = (int)blk.size();
+  CUDA_TRY(cudaMalloc(&d_blk_prob, sizeof(int) * blk.size()));
+  CUDA_TRY(cudaMemcpy(d_blk_prob, blk.data(), sizeof(int) * blk.size(), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaStreamSynchronize(stream));
+  return DIRAC_OK;
+}
+
+void Engine::release() {
+  cudaStreamSynchronize(stream);
+  for (cudaEvent_t ev : ev_pool) cudaEventDestroy(ev);
+  ev_pool.clear();
+  if (tab_ev) cudaEventDestroy(tab_ev);
+  cudaFree(vec_mem);
+  for (HostProblem& q : P) cudaFree(q.V);
+  cudaFree(d_st);
+  cudaFreeHost(h_st);
+  cudaFree(d_partials);
+  cudaFree(d_blk_prob);
+  cudaFree(d_step);
+  cudaFree(d_tab);
+  cudaFreeHost(h_tab);
+  cudaFree(psi_own);
+}
+
+dirac_status Engine::set_stream(cudaStream_t s) {
+  if (s != stream) {
+    // order the new stream after everything already queued on the old one
+    cudaEvent_t ev;
+    CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventRecord(ev, stream));
+    CUDA_TRY(cudaStreamWaitEvent(s, ev, 0));
+    CUDA_TRY(cudaEventDestroy(ev));
+    stream = s;
+  }
+  return DIRAC_OK;
+}
+
+dirac_status Engine::set_fields(int b, const double* V_dev, double ax, double ay, double shift) {
+  if (b < 0 || b >= nprob()) return fail(DIRAC_EINVAL, "problem index %d out of range", b);
+  if (!std::isfinite(ax) || !std::isfinite(ay) || !std::isfinite(shift))
+    return fail(DIRAC_EINVAL, "non-finite field scalar");
+  HostProblem& q = P[b];
+  if (V_dev) {
+    const bool f32 = precision != DIRAC_FP64;
+    if (!q.V) CUDA_TRY(cudaMalloc(&q.V, (f32 ? sizeof(float) : sizeof(double)) * q.n));
+    if (f32) {
+      to_float_kernel<<<256, 256, 0, stream>>>(V_dev, static_cast<float*>(q.V), q.n);
+      ++launches;
+      CUDA_TRY(cudaGetLastError());
+    } else {
+      CUDA_TRY(cudaMemcpyAsync(q.V, V_dev, sizeof(double) * q.n, cudaMemcpyDeviceToDevice, stream));
+    }
+    double* mm = d_partials;   // two doubles of scratch (rewritten by every pass)
+    minmax_kernel<<<1, 256, 0, stream>>>(V_dev, q.n, mm);
+    ++launches;
+    CUDA_TRY(cudaGetLastError());
+    double h[2];
+    CUDA_TRY(cudaMemcpyAsync(h, mm, sizeof(h), cudaMemcpyDeviceToHost, stream));
+    CUDA_TRY(cudaStreamSynchronize(stream));
+    if (!std::isfinite(h[0]) || !std::isfinite(h[1])) return fail(DIRAC_EINVAL, "V has non-finite entries");
+    q.vmin = h[0];
+    q.vmax = h[1];
+    q.has_v = true;
+  } else {
+    q.has_v = false;
+    q.vmin = q.vmax = 0.0;
+  }
+  q.ax = ax;
+  q.ay = ay;
+  q.shift = shift;
+  q.fields_set = true;
+  need_probe = true;
+  return DIRAC_OK;
+}
+
+dirac_status Engine::run(vec4* const* psi, int nsteps, double dt, int m, double tol, const double* a_xy) {
+  const int np = nprob();
+  for (int b = 0; b < np; ++b) {
+    if (!P[b].fields_set) return fail(DIRAC_ESTATE, "fields of problem %d not set", b);
+    if (!psi[b] || !aligned32(psi[b])) return fail(DIRAC_EINVAL, "psi of problem %d null or not 32-byte aligned", b);
+  }
+  if (m < 1 || m > m_max) return fail(DIRAC_EINVAL, "m = %d outside 1..m_max = %d", m, m_max);
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(DIRAC_EINVAL, "dt must be finite and > 0");
+  if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(DIRAC_EINVAL, "tol must be finite and >= 0");
+  if (nsteps < 0) return fail(DIRAC_EINVAL, "nsteps < 0");
+  if (nsteps == 0) return DIRAC_OK;
+  if (a_xy)
+    for (long long k = 0; k < 2LL * nsteps * np; ++k)
+      if (!std::isfinite(a_xy[k])) return fail(DIRAC_EINVAL, "non-finite vector potential in the schedule");
+  const int th = precision == DIRAC_FP64 ? 32 : shape.th;
+  // tile list for this tile height
+  int tt = 0;
+  for (HostProblem& q : P) {
+    q.ntiles = tiles_of(q.nx, q.ny, th);
+    q.tile_begin = tt;
+    tt += q.ntiles;
+  }
+  total_tiles = tt;
+  // tables: problems, Chebyshev parameters, fields of every step
+  const int nfield = a_xy ? nsteps * np : np;
+  const size_t off_cheb = align256(sizeof(Problem) * np);
+  const size_t off_field = off_cheb + align256(sizeof(ChebParams) * np);
+  const size_t bytes = off_field + align256(sizeof(FieldStep) * nfield);
+  if (tab_ev_live) CUDA_TRY(cudaEventSynchronize(tab_ev));   // staging free again
+  if (bytes > tab_cap) {
+    CUDA_TRY(cudaStreamSynchronize(stream));
+    cudaFree(d_tab);
+    cudaFreeHost(h_tab);
+    d_tab = h_tab = nullptr;
+    tab_cap = 0;
+    CUDA_TRY(cudaMalloc(&d_tab, bytes));
+    CUDA_TRY(cudaMallocHost(&h_tab, bytes));
+    tab_cap = bytes;
+  }
+  char* hb = static_cast<char*>(h_tab);
+  char* db = static_cast<char*>(d_tab);
+  Problem* hp = reinterpret_cast<Problem*>(hb);
+  ChebParams* hc = reinterpret_cast<ChebParams*>(hb + off_cheb);
+  FieldStep* hf = reinterpret_cast<FieldStep*>(hb + off_field);
+  const double kfac = (order == 2) ? 2.0 : 12.0;
+  const double mcc = mass * c * c;
+  bool hasv = false;
+  for (int b = 0; b < np; ++b) {
+    HostProblem& q = P[b];
+    double axm = std::fabs(q.ax), aym = std::fabs(q.ay);
+    if (a_xy) {
+      axm = aym = 0.0;
+      for (int s = 0; s < nsteps; ++s) {
+        axm = std::max(axm, std::fabs(a_xy[2 * ((size_t)s * np + b)]));
+        aym = std::max(aym, std::fabs(a_xy[2 * ((size_t)s * np + b) + 1]));
+      }
+      q.ax = a_xy[2 * ((size_t)(nsteps - 1) * np + b)];
+      q.ay = a_xy[2 * ((size_t)(nsteps - 1) * np + b) + 1];
+    }
+    double c0, half;
+    spectral_interval(order, q.dx, q.dy, mass, c, axm, aym, q.has_v ? q.vmin : 0.0,
+                      q.has_v ? q.vmax : 0.0, q.shift, c0, half);
+    dirac_status s = make_cheb(c0, half, dt, q.shift, hc[b]);
+    if (s != DIRAC_OK) return s;
+    Problem& d = hp[b];
+    std::memset(&d, 0, sizeof(d));
+    d.nx = q.nx; d.ny = q.ny; d.tiles_x = q.tiles_x; d.tile_begin = q.tile_begin; d.ntiles = q.ntiles;
+    d.rblk_begin = q.rblk_begin; d.rblk_count = q.rblk_count;
+    d.psi = psi[b];
+    d.basis = q.basis; d.ybuf0 = q.ybuf[0]; d.ybuf1 = q.ybuf[1];
+    d.V = q.has_v ? q.V : nullptr;
+    d.st = d_st + b;
+    d.partials = d_partials + 3 * q.slot_off;
+    d.cheb = reinterpret_cast<const ChebParams*>(db + off_cheb) + b;
+    d.kx = c / (kfac * q.dx);
+    d.ky = c / (kfac * q.dy);
+    d.kxf = (float)d.kx;
+    d.kyf = (float)d.ky;
+    d.shift = q.shift;
+    d.probe_coef = make_coef(1.0, 0.0, 0.0, mcc - q.shift, -mcc - q.shift);
+    hasv = hasv || q.has_v;
+  }
+  for (int k = 0; k < nfield; ++k) {
+    const int b = k % np;
+    const double ax = a_xy ? a_xy[2 * (size_t)k] : P[b].ax;
+    const double ay = a_xy ? a_xy[2 * (size_t)k + 1] : P[b].ay;
+    FieldStep& f = hf[k];
+    f.cAx = c * ax;   // electron: p - qA = p + A
+    f.cAy = c * ay;
+    f.cAxf = (float)f.cAx;
+    f.cAyf = (float)f.cAy;
+    f.pad0 = f.pad1 = 0.f;
+  }
+  CUDA_TRY(cudaMemcpyAsync(d_tab, h_tab, bytes, cudaMemcpyHostToDevice, stream));
+  CUDA_TRY(cudaEventRecord(tab_ev, stream));
+  tab_ev_live = true;
+  CUDA_TRY(cudaMemsetAsync(d_step, 0, sizeof(int), stream));
+
+  LaunchParams lp;
+  std::memset(&lp, 0, sizeof(lp));
+  lp.probs = reinterpret_cast<const Problem*>(d_tab);
+  lp.states = d_st;
+  lp.fields = reinterpret_cast<const FieldStep*>(db + off_field);
+  lp.fstride = a_xy ? np : 0;
+  lp.nprob = np;
+  lp.total_tiles = total_tiles;
+  lp.m = m;
+  lp.mcc = mcc;
+  lp.dt = dt;
+  lp.tol = tol;
+  lp.step = d_step;
+  lp.redo_budget = redo_budget(precision, m);
+  lp.kappa_redo = kappa_redo(precision);
+  RecombParams rp;
+  rp.probs = lp.probs;
+  rp.blk_prob = d_blk_prob;
+  rp.step = d_step;
+  rp.redo_budget = lp.redo_budget;
+  LaunchShape ls = shape;
+  ls.th = th;
+  const bool diri = boundary == DIRAC_DIRICHLET;
+  for (int s = 0; s < nsteps; ++s) {
+    if (need_probe) {
+      lp.pass = 1;
+      lp.probe = 1;
+      CUDA_TRY(mark(KIND_PASS));
+      CUDA_TRY(launch_pass(precision, order, diri, hasv, lp, ls, stream));
+      ++launches;
+      lp.probe = 0;
+      need_probe = false;
+    }
+    // m passes plus the spare launches for re-runs; every problem runs its
+    // own next pass and launches with nothing left to do exit at once
+    for (int i = 1; i <= m + lp.redo_budget; ++i) {
+      lp.pass = i;
+      CUDA_TRY(mark(KIND_PASS));
+      CUDA_TRY(launch_pass(precision, order, diri, hasv, lp, ls, stream));
+      ++launches;
+    }
+    CUDA_TRY(mark(KIND_RECOMBINE));
+    CUDA_TRY(launch_recombine(precision, rp, rgrid, stream));
+    ++launches;
+    CUDA_TRY(mark(KIND_END));
+  }
+  return DIRAC_OK;
+}
+
+dirac_status Engine::read_state(dirac_step_info* info) {
+  const int np = nprob();
+  CUDA_TRY(cudaMemcpyAsync(h_st, d_st, sizeof(DevState) * np, cudaMemcpyDeviceToHost, stream));
+  CUDA_TRY(cudaStreamSynchronize(stream));
+  bool bad = false;
+  for (int b = 0; b < np; ++b) bad = bad || h_st[b].error;
+  if (bad) {
+    const int zero[2] = {0, 0};
+    for (int b = 0; b < np; ++b) {
+      if (!h_st[b].error) continue;
+      CUDA_TRY(cudaMemcpyAsync(&d_st[b].stopped, &zero[0], sizeof(int), cudaMemcpyHostToDevice, stream));
+      CUDA_TRY(cudaMemcpyAsync(&d_st[b].error, &zero[1], sizeof(int), cudaMemcpyHostToDevice, stream));
+    }
+    CUDA_TRY(cudaStreamSynchronize(stream));
+    need_probe = true;
+  }
+  if (info) {
+    for (int b = 0; b < np; ++b) {
+      const DevState& h = h_st[b];
+      dirac_step_info& o = info[b];
+      std::memset(&o, 0, sizeof(o));
+      o.k_used = h.k_used;
+      o.breakdown = h.breakdown;
+      o.err_est = h.err_est;
+      o.cum_err = h.cum_err;
+      o.norm = h.psi_norm;
+      o.energy = h.energy;
+      o.kappa_max = h.kappa_max;
+      for (int j = 0; j < h.k_used && j < DIRAC_KRYLOV_MAX; ++j) {
+        o.alpha[j] = h.alpha[j + 1];
+        o.beta[j] = h.beta[j + 1];
+      }
+    }
+  }
+  if (bad) return fail(DIRAC_ENONFINITE, "non-finite value in a Lanczos reduction; psi left unchanged");
+  return DIRAC_OK;
+}
+
+dirac_status profile_read(Engine& e, double* ms, long long* launches) {
+  for (int k = 0; k < DIRAC_KERNEL_KINDS; ++k) { ms[k] = 0.0; launches[k] = 0; }
+  if (e.ev_used > 0) CUDA_TRY(cudaEventSynchronize(e.ev_pool[e.ev_used - 1]));
+  for (size_t j = 0; j + 1 < e.ev_used; ++j) {
+    const int k = e.ev_kind[j];
+    if (k < 0) continue;
+    float t = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&t, e.ev_pool[j], e.ev_pool[j + 1]));
+    ms[k] += t;
+    launches[k] += 1;
+  }
+  e.ev_used = 0;
+  return DIRAC_OK;
+}
+
 }  // namespace
+
+struct dirac_ctx {
+  Engine e;
+};
+
+struct dirac_batch {
+  Engine e;
+};
 
 extern "C" {
 
@@ -385,42 +683,16 @@ dirac_status dirac_create(dirac_ctx** out, int nx, int ny, double dx, double dy,
   g_err[0] = 0;
   if (!out) return fail(DIRAC_EINVAL, "null output pointer");
   *out = nullptr;
-  if (nx < 1 || ny < 1) return fail(DIRAC_EINVAL, "grid %d x %d must be at least 1 x 1", nx, ny);
-  if (!(dx > 0) || !(dy > 0) || !std::isfinite(dx) || !std::isfinite(dy))
-    return fail(DIRAC_EINVAL, "dx, dy must be finite and > 0");
-  if (!(c > 0) || !std::isfinite(c)) return fail(DIRAC_EINVAL, "c must be finite and > 0");
-  if (!(mass >= 0) || !std::isfinite(mass)) return fail(DIRAC_EINVAL, "mass must be finite and >= 0");
-  if (stencil_order != 2 && stencil_order != 4) return fail(DIRAC_EINVAL, "stencil_order must be 2 or 4");
-  if (boundary != DIRAC_PERIODIC && boundary != DIRAC_DIRICHLET) return fail(DIRAC_EINVAL, "bad boundary");
-  if (precision != DIRAC_FP64 && precision != DIRAC_MIXED)
-    return fail(DIRAC_EINVAL, "precision must be DIRAC_FP64 or DIRAC_MIXED");
-  if (m_max < 1 || m_max > DIRAC_KRYLOV_MAX) return fail(DIRAC_EINVAL, "m_max must be 1..%d", DIRAC_KRYLOV_MAX);
-  const long long n = (long long)nx * ny;
-  if (n > (1LL << 31)) return fail(DIRAC_EINVAL, "grid too large");
-
+  dirac_status s = check_grid(nx, ny, dx, dy);
+  if (s == DIRAC_OK) s = check_common(mass, c, stencil_order, boundary, precision, m_max);
+  if (s != DIRAC_OK) return s;
   dirac_ctx* ctx = new (std::nothrow) dirac_ctx;
   if (!ctx) return fail(DIRAC_ENOMEM, "host allocation failed");
-  ctx->nx = nx; ctx->ny = ny; ctx->dx = dx; ctx->dy = dy; ctx->mass = mass; ctx->c = c;
-  ctx->order = stencil_order; ctx->boundary = boundary; ctx->precision = precision;
-  ctx->m_max = m_max; ctx->stream = (cudaStream_t)cuda_stream; ctx->n_sites = n;
-  ctx->grid = dim3((nx + TILE - 1) / TILE, (ny + TILE - 1) / TILE);
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, dev);
-  const size_t vb = (size_t)n * site_bytes(precision);
-  const int nbasis = std::max(1, m_max - 1);
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->basis, vb * nbasis);
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->ybuf[0], vb);
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->ybuf[1], vb);
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->st, sizeof(DevState));
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->partials, sizeof(double) * 3 * (size_t)ctx->grid.x * ctx->grid.y);
-  if (e == cudaSuccess) e = cudaMallocHost(&ctx->st_host, sizeof(DevState));
-  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->st, 0, sizeof(DevState), ctx->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-  if (e != cudaSuccess) {
-    const bool oom = (e == cudaErrorMemoryAllocation);
-    dirac_destroy(ctx);
-    return fail(oom ? DIRAC_ENOMEM : DIRAC_ECUDA, "create: %s", cudaGetErrorString(e));
+  s = ctx->e.init(1, &nx, &ny, &dx, &dy, mass, c, stencil_order, boundary, precision, m_max, cuda_stream);
+  if (s != DIRAC_OK) {
+    ctx->e.release();
+    delete ctx;
+    return s;
   }
   *out = ctx;
   return DIRAC_OK;
@@ -428,79 +700,26 @@ dirac_status dirac_create(dirac_ctx** out, int nx, int ny, double dx, double dy,
 
 void dirac_destroy(dirac_ctx* ctx) {
   if (!ctx) return;
-  cudaStreamSynchronize(ctx->stream);
-  for (cudaEvent_t ev : ctx->ev_pool) cudaEventDestroy(ev);
-  cudaFree(ctx->basis);
-  cudaFree(ctx->ybuf[0]);
-  cudaFree(ctx->ybuf[1]);
-  cudaFree(ctx->psi_own);
-  cudaFree(ctx->V);
-  cudaFree(ctx->st);
-  cudaFree(ctx->partials);
-  cudaFreeHost(ctx->st_host);
+  ctx->e.release();
   delete ctx;
 }
 
 dirac_status dirac_set_stream(dirac_ctx* ctx, void* cuda_stream) {
   if (!ctx) return fail(DIRAC_EINVAL, "null context");
-  if ((cudaStream_t)cuda_stream != ctx->stream) {
-    // order the new stream after everything already queued on the old one
-    cudaEvent_t ev;
-    CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    CUDA_TRY(cudaEventRecord(ev, ctx->stream));
-    CUDA_TRY(cudaStreamWaitEvent((cudaStream_t)cuda_stream, ev, 0));
-    CUDA_TRY(cudaEventDestroy(ev));
-    ctx->stream = (cudaStream_t)cuda_stream;
-  }
-  return DIRAC_OK;
+  return ctx->e.set_stream((cudaStream_t)cuda_stream);
 }
 
 dirac_status dirac_set_fields(dirac_ctx* ctx, const double* V_dev, double A_x, double A_y,
                               double energy_shift) {
   if (!ctx) return fail(DIRAC_EINVAL, "null context");
-  if (!std::isfinite(A_x) || !std::isfinite(A_y) || !std::isfinite(energy_shift))
-    return fail(DIRAC_EINVAL, "non-finite field scalar");
-  if (V_dev) {
-    const bool f32 = ctx->precision != DIRAC_FP64;
-    if (!ctx->V) CUDA_TRY(cudaMalloc(&ctx->V, (f32 ? sizeof(float) : sizeof(double)) * ctx->n_sites));
-    if (f32) {
-      to_float_kernel<<<256, 256, 0, ctx->stream>>>(V_dev, static_cast<float*>(ctx->V), ctx->n_sites);
-      ++ctx->launches;
-      CUDA_TRY(cudaGetLastError());
-    } else {
-      CUDA_TRY(cudaMemcpyAsync(ctx->V, V_dev, sizeof(double) * ctx->n_sites, cudaMemcpyDeviceToDevice, ctx->stream));
-    }
-    double* mm = nullptr;
-    CUDA_TRY(cudaMalloc(&mm, 2 * sizeof(double)));
-    minmax_kernel<<<1, 256, 0, ctx->stream>>>(V_dev, ctx->n_sites, mm);
-    ++ctx->launches;
-    double h[2];
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h, mm, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    cudaFree(mm);
-    if (e != cudaSuccess) return fail(DIRAC_ECUDA, "set_fields: %s", cudaGetErrorString(e));
-    if (!std::isfinite(h[0]) || !std::isfinite(h[1])) return fail(DIRAC_EINVAL, "V has non-finite entries");
-    ctx->vmin = h[0];
-    ctx->vmax = h[1];
-    ctx->has_v = true;
-  } else {
-    ctx->has_v = false;
-    ctx->vmin = ctx->vmax = 0.0;
-  }
-  ctx->ax = A_x;
-  ctx->ay = A_y;
-  ctx->shift = energy_shift;
-  ctx->fields_set = true;
-  ctx->need_probe = true;
-  return DIRAC_OK;
+  return ctx->e.set_fields(0, V_dev, A_x, A_y, energy_shift);
 }
 
 dirac_status dirac_set_vector_potential(dirac_ctx* ctx, double A_x, double A_y) {
   if (!ctx) return fail(DIRAC_EINVAL, "null context");
   if (!std::isfinite(A_x) || !std::isfinite(A_y)) return fail(DIRAC_EINVAL, "non-finite vector potential");
-  ctx->ax = A_x;
-  ctx->ay = A_y;
+  ctx->e.P[0].ax = A_x;
+  ctx->e.P[0].ay = A_y;
   return DIRAC_OK;
 }
 
@@ -511,32 +730,32 @@ dirac_status dirac_lanczos_step(dirac_ctx* ctx, void* psi_dev, double dt, int m,
 
 dirac_status dirac_lanczos_steps(dirac_ctx* ctx, void* psi_dev, int nsteps, double dt, int m,
                                  double tol, const double* A_xy_host, dirac_step_info* info) {
-  dirac_status s = check_step_args(ctx, psi_dev, dt, m, tol, true);
+  if (!ctx) return fail(DIRAC_EINVAL, "null context");
+  if (!psi_dev) return fail(DIRAC_EINVAL, "null psi");
+  vec4* psi = static_cast<vec4*>(psi_dev);
+  dirac_status s = ctx->e.run(&psi, nsteps, dt, m, tol, A_xy_host);
   if (s != DIRAC_OK) return s;
-  if (nsteps < 0) return fail(DIRAC_EINVAL, "nsteps < 0");
-  s = run_steps(ctx, (vec4*)psi_dev, nsteps, dt, m, tol, A_xy_host);
-  if (s != DIRAC_OK) return s;
-  if (info) return read_state(ctx, info);
+  if (info) return ctx->e.read_state(info);
   return DIRAC_OK;
 }
 
 dirac_status dirac_propagate_host(dirac_ctx* ctx, void* psi_host, int nsteps, double dt, int m,
                                   double tol, const double* A_xy_host, dirac_step_info* info) {
-  dirac_status s = check_step_args(ctx, psi_host, dt, m, tol, false);
+  if (!ctx) return fail(DIRAC_EINVAL, "null context");
+  if (!psi_host) return fail(DIRAC_EINVAL, "null psi");
+  Engine& e = ctx->e;
+  const size_t bytes = (size_t)e.P[0].n * sizeof(vec4);
+  if (!e.psi_own) CUDA_TRY(cudaMalloc(&e.psi_own, bytes));
+  CUDA_TRY(cudaMemcpyAsync(e.psi_own, psi_host, bytes, cudaMemcpyHostToDevice, e.stream));
+  dirac_status s = e.run(&e.psi_own, nsteps, dt, m, tol, A_xy_host);
   if (s != DIRAC_OK) return s;
-  if (nsteps < 0) return fail(DIRAC_EINVAL, "nsteps < 0");
-  const size_t bytes = (size_t)ctx->n_sites * sizeof(vec4);
-  if (!ctx->psi_own) CUDA_TRY(cudaMalloc(&ctx->psi_own, bytes));
-  CUDA_TRY(cudaMemcpyAsync(ctx->psi_own, psi_host, bytes, cudaMemcpyHostToDevice, ctx->stream));
-  s = run_steps(ctx, ctx->psi_own, nsteps, dt, m, tol, A_xy_host);
-  if (s != DIRAC_OK) return s;
-  CUDA_TRY(cudaMemcpyAsync(psi_host, ctx->psi_own, bytes, cudaMemcpyDeviceToHost, ctx->stream));
-  return read_state(ctx, info);
+  CUDA_TRY(cudaMemcpyAsync(psi_host, e.psi_own, bytes, cudaMemcpyDeviceToHost, e.stream));
+  return e.read_state(info);
 }
 
 dirac_status dirac_sync(dirac_ctx* ctx) {
   if (!ctx) return fail(DIRAC_EINVAL, "null context");
-  return read_state(ctx, nullptr);
+  return ctx->e.read_state(nullptr);
 }
 
 double dirac_pulse_sin2_mean(double t0, double dt, double a0, double omega, double duration) {
@@ -552,29 +771,97 @@ double dirac_pulse_sin2_mean(double t0, double dt, double a0, double omega, doub
   return a0 * (0.5 * integ(omega) - 0.25 * integ(omega + W) - 0.25 * integ(omega - W)) / dt;
 }
 
-long long dirac_kernel_launches(const dirac_ctx* ctx) { return ctx ? ctx->launches : 0; }
+long long dirac_kernel_launches(const dirac_ctx* ctx) { return ctx ? ctx->e.launches : 0; }
 
 dirac_status dirac_profile_enable(dirac_ctx* ctx, int enable) {
   if (!ctx) return fail(DIRAC_EINVAL, "null context");
-  ctx->profiling = enable != 0;
+  ctx->e.profiling = enable != 0;
   return DIRAC_OK;
 }
 
 dirac_status dirac_profile_read(dirac_ctx* ctx, double* ms, long long* launches) {
   if (!ctx || !ms || !launches) return fail(DIRAC_EINVAL, "null argument");
-  for (int k = 0; k < DIRAC_KERNEL_KINDS; ++k) { ms[k] = 0.0; launches[k] = 0; }
-  if (ctx->ev_used > 0) CUDA_TRY(cudaEventSynchronize(ctx->ev_pool[ctx->ev_used - 1]));
-  for (size_t j = 0; j + 1 < ctx->ev_used; ++j) {
-    const int k = ctx->ev_kind[j];
-    if (k < 0) continue;
-    float t = 0.f;
-    CUDA_TRY(cudaEventElapsedTime(&t, ctx->ev_pool[j], ctx->ev_pool[j + 1]));
-    ms[k] += t;
-    launches[k] += 1;
+  return profile_read(ctx->e, ms, launches);
+}
+
+// ----------------------------- batches -------------------------------------
+
+dirac_status dirac_batch_create(dirac_batch** out, int n_problems, const int* nx, const int* ny,
+                                const double* dx, const double* dy, double mass, double c,
+                                int stencil_order, int boundary, int precision, int m_max,
+                                void* cuda_stream) {
+  g_err[0] = 0;
+  if (!out) return fail(DIRAC_EINVAL, "null output pointer");
+  *out = nullptr;
+  if (n_problems < 1 || !nx || !ny || !dx || !dy) return fail(DIRAC_EINVAL, "need n_problems >= 1 and sizes");
+  for (int b = 0; b < n_problems; ++b) {
+    dirac_status s = check_grid(nx[b], ny[b], dx[b], dy[b]);
+    if (s != DIRAC_OK) return s;
   }
-  ctx->ev_used = 0;
+  dirac_status s = check_common(mass, c, stencil_order, boundary, precision, m_max);
+  if (s != DIRAC_OK) return s;
+  dirac_batch* bt = new (std::nothrow) dirac_batch;
+  if (!bt) return fail(DIRAC_ENOMEM, "host allocation failed");
+  s = bt->e.init(n_problems, nx, ny, dx, dy, mass, c, stencil_order, boundary, precision, m_max, cuda_stream);
+  if (s != DIRAC_OK) {
+    bt->e.release();
+    delete bt;
+    return s;
+  }
+  *out = bt;
   return DIRAC_OK;
 }
+
+void dirac_batch_destroy(dirac_batch* bt) {
+  if (!bt) return;
+  bt->e.release();
+  delete bt;
+}
+
+dirac_status dirac_batch_set_fields(dirac_batch* bt, int problem, const double* V_dev, double A_x,
+                                    double A_y, double energy_shift) {
+  if (!bt) return fail(DIRAC_EINVAL, "null batch");
+  return bt->e.set_fields(problem, V_dev, A_x, A_y, energy_shift);
+}
+
+dirac_status dirac_batch_set_launch_shape(dirac_batch* bt, int tile_height, int ctas_per_sm) {
+  if (!bt) return fail(DIRAC_EINVAL, "null batch");
+  if (tile_height != 16 && tile_height != 32) return fail(DIRAC_EINVAL, "tile height must be 16 or 32");
+  if (ctas_per_sm < 0) return fail(DIRAC_EINVAL, "ctas_per_sm < 0");
+  bt->e.shape.th = tile_height;
+  bt->e.shape.cta_cap = ctas_per_sm;
+  return DIRAC_OK;
+}
+
+dirac_status dirac_batch_steps(dirac_batch* bt, void* const* psi_dev, int nsteps, double dt, int m,
+                               double tol, const double* A_xy_host, dirac_step_info* info) {
+  if (!bt) return fail(DIRAC_EINVAL, "null batch");
+  if (!psi_dev) return fail(DIRAC_EINVAL, "null psi table");
+  dirac_status s = bt->e.run(reinterpret_cast<vec4* const*>(psi_dev), nsteps, dt, m, tol, A_xy_host);
+  if (s != DIRAC_OK) return s;
+  if (info) return bt->e.read_state(info);
+  return DIRAC_OK;
+}
+
+dirac_status dirac_batch_sync(dirac_batch* bt, dirac_step_info* info) {
+  if (!bt) return fail(DIRAC_EINVAL, "null batch");
+  return bt->e.read_state(info);
+}
+
+dirac_status dirac_batch_profile_enable(dirac_batch* bt, int enable) {
+  if (!bt) return fail(DIRAC_EINVAL, "null batch");
+  bt->e.profiling = enable != 0;
+  return DIRAC_OK;
+}
+
+dirac_status dirac_batch_profile_read(dirac_batch* bt, double* ms, long long* launches) {
+  if (!bt || !ms || !launches) return fail(DIRAC_EINVAL, "null argument");
+  return profile_read(bt->e, ms, launches);
+}
+
+long long dirac_batch_kernel_launches(const dirac_batch* bt) { return bt ? bt->e.launches : 0; }
+
+// ----------------------------- test hook -----------------------------------
 
 dirac_status dirac_debug_tridiag_expm(const double* alpha, const double* beta, int k, double dt,
                                       double lo, double hi, double* v_re, double* v_im) {
@@ -610,10 +897,10 @@ dirac_status dirac_debug_tridiag_expm(const double* alpha, const double* beta, i
 // that owns every device allocation and forbids libraries from calling
 // cudaMalloc, a fixed memory budget decided up front, or a per-step loop in
 // which the latency or the failure of an allocation is not acceptable.  The
-// step keeps its whole workspace (scalar block, per-CTA partial sums, the two
-// y^ fields and the Krylov basis) in one file-scope device array of fixed
-// size, shared by every call in the process, and calls no cudaMalloc,
-// cudaFree or other allocating routine (host or device).
+// step keeps its whole workspace (problem table, scalar block, per-CTA
+// partial sums, the two y^ fields and the Krylov basis) in one file-scope
+// device array of fixed size, shared by every call in the process, and calls
+// no cudaMalloc, cudaFree or other allocating routine (host or device).
 // ===========================================================================
 namespace {
 
@@ -639,48 +926,6 @@ dirac_status noalloc_scratch(unsigned char** out) {
   return DIRAC_OK;
 }
 
-size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
-
-// Chebyshev coefficients as make_cheb, with stack storage only.
-dirac_status noalloc_cheb(double c0, double half, double dt, double shift, ChebParams& cp) {
-  const double R = half * dt;
-  if (!(R > 0.0) || R > 90.0)
-    return fail(DIRAC_EINVAL, "dt * ||H|| = %.3g outside (0, 90]: take smaller steps", R);
-  constexpr int NJ = 512;
-  double j[NJ + 2];
-  const int start = 2 * ((std::max(CHEB_MAX, (int)R) + 40 + (int)std::sqrt(40.0 * std::max(R, 1.0))) / 2);
-  if (start > NJ) return fail(DIRAC_EINVAL, "dt too large");
-  for (int k = 0; k <= start + 1; ++k) j[k] = 0.0;
-  j[start] = 1e-300;
-  for (int k = start; k >= 1; --k) {
-    j[k - 1] = (2.0 * k / R) * j[k] - j[k + 1];
-    if (std::fabs(j[k - 1]) > 1e250)
-      for (int t = k - 1; t <= start; ++t) j[t] *= 1e-250;
-  }
-  double norm = j[0];
-  for (int k = 2; k <= start; k += 2) norm += 2.0 * j[k];
-  int n = 2;
-  for (int k = 0; k < CHEB_MAX; ++k)
-    if (std::fabs(j[k] / norm) > 1e-18 || k <= (int)R + 1) n = k + 1;
-  if (n >= CHEB_MAX) return fail(DIRAC_EINVAL, "Chebyshev expansion needs more than %d terms", CHEB_MAX);
-  cp.n = std::max(n, 2);
-  cp.c0 = c0;
-  cp.inv_half = 1.0 / half;
-  const double ph = -(c0 + shift) * dt;
-  cp.ph_re = std::cos(ph);
-  cp.ph_im = std::sin(ph);
-  for (int k = 0; k < CHEB_MAX; ++k) {
-    const double a = (k == 0 ? 1.0 : 2.0) * (k < cp.n ? j[k] / norm : 0.0);
-    switch (k & 3) {
-      case 0: cp.cr[k] = a;  cp.ci[k] = 0.0; break;
-      case 1: cp.cr[k] = 0.0; cp.ci[k] = -a; break;
-      case 2: cp.cr[k] = -a; cp.ci[k] = 0.0; break;
-      default: cp.cr[k] = 0.0; cp.ci[k] = a; break;
-    }
-  }
-  return DIRAC_OK;
-}
-
 }  // namespace
 
 extern "C" size_t dirac_noalloc_scratch_bytes(void) { return NOALLOC_SCRATCH_BYTES; }
@@ -689,28 +934,29 @@ extern "C" dirac_status dirac_lanczos_step_noalloc(const dirac_problem* pb, void
                                                    int m, double tol, void* cuda_stream,
                                                    dirac_step_info* info) {
   if (!pb || !psi_dev) return fail(DIRAC_EINVAL, "null argument");
-  const int nx = pb->nx, ny = pb->ny;
-  if (nx < 1 || ny < 1) return fail(DIRAC_EINVAL, "grid %d x %d must be at least 1 x 1", nx, ny);
-  if (!(pb->dx > 0) || !(pb->dy > 0) || !std::isfinite(pb->dx) || !std::isfinite(pb->dy))
-    return fail(DIRAC_EINVAL, "dx, dy must be finite and > 0");
-  if (!(pb->c > 0) || !std::isfinite(pb->c)) return fail(DIRAC_EINVAL, "c must be finite and > 0");
-  if (!(pb->mass >= 0) || !std::isfinite(pb->mass)) return fail(DIRAC_EINVAL, "mass must be finite and >= 0");
-  if (pb->stencil_order != 2 && pb->stencil_order != 4) return fail(DIRAC_EINVAL, "stencil_order must be 2 or 4");
-  if (pb->boundary != DIRAC_PERIODIC && pb->boundary != DIRAC_DIRICHLET) return fail(DIRAC_EINVAL, "bad boundary");
+  dirac_status s = check_grid(pb->nx, pb->ny, pb->dx, pb->dy);
+  if (s == DIRAC_OK) s = check_common(pb->mass, pb->c, pb->stencil_order, pb->boundary, DIRAC_FP64, m);
+  if (s != DIRAC_OK) return s;
   if (!std::isfinite(pb->A_x) || !std::isfinite(pb->A_y) || !std::isfinite(pb->energy_shift))
     return fail(DIRAC_EINVAL, "non-finite field scalar");
-  if (m < 1 || m > DIRAC_KRYLOV_MAX) return fail(DIRAC_EINVAL, "m = %d outside 1..%d", m, DIRAC_KRYLOV_MAX);
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(DIRAC_EINVAL, "dt must be finite and > 0");
   if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(DIRAC_EINVAL, "tol must be finite and >= 0");
   if (!aligned32(psi_dev)) return fail(DIRAC_EINVAL, "psi must be 32-byte aligned");
 
-  // scratch layout: DevState | partials | y^[2] | basis[m-1]
+  // scratch layout: Problem | ChebParams | FieldStep | step counter and block
+  //                 map | DevState | partials | y^[2] | basis[m-1]
+  const int nx = pb->nx, ny = pb->ny;
   const long long n = (long long)nx * ny;
-  const dim3 grid((nx + TILE - 1) / TILE, (ny + TILE - 1) / TILE);
-  const size_t ncta = (size_t)grid.x * grid.y;
-  const size_t field = round256((size_t)n * sizeof(vec4));
-  const size_t off_part = round256(sizeof(DevState));
-  const size_t off_y = off_part + round256(3 * sizeof(double) * ncta);
+  const int tiles_x = (nx + TILE_W - 1) / TILE_W;
+  const int ntiles = tiles_of(nx, ny, 32);
+  constexpr int RB_MAX = 64;                   // recombination blocks
+  const size_t field = align256((size_t)n * sizeof(vec4));
+  const size_t off_cheb = align256(sizeof(Problem));
+  const size_t off_field = off_cheb + align256(sizeof(ChebParams));
+  const size_t off_step = off_field + align256(sizeof(FieldStep));
+  const size_t off_st = off_step + align256(sizeof(int) * (1 + RB_MAX));
+  const size_t off_part = off_st + align256(sizeof(DevState));
+  const size_t off_y = off_part + align256(3 * sizeof(double) * ntiles);
   const size_t off_basis = off_y + 2 * field;
   const size_t need = off_basis + (size_t)std::max(1, m - 1) * field;
   if (need > NOALLOC_SCRATCH_BYTES)
@@ -718,88 +964,103 @@ extern "C" dirac_status dirac_lanczos_step_noalloc(const dirac_problem* pb, void
                 "holds %zu bytes (use dirac_create for larger problems)", nx, ny, m, need,
                 NOALLOC_SCRATCH_BYTES);
   unsigned char* base = nullptr;
-  dirac_status s = noalloc_scratch(&base);
+  s = noalloc_scratch(&base);
   if (s != DIRAC_OK) return s;
   cudaStream_t stream = (cudaStream_t)cuda_stream;
-  DevState* st = reinterpret_cast<DevState*>(base);
+  int n_sm = 0, dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  DevState* st = reinterpret_cast<DevState*>(base + off_st);
   double* partials = reinterpret_cast<double*>(base + off_part);
-  vec4* ybuf[2] = {reinterpret_cast<vec4*>(base + off_y), reinterpret_cast<vec4*>(base + off_y + field)};
-  vec4* basis = reinterpret_cast<vec4*>(base + off_basis);
-  vec4* psi = static_cast<vec4*>(psi_dev);
-
-  // the scratch keeps the previous call's contents: restart the scalar block
-  CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(DevState), stream));
+  int* step = reinterpret_cast<int*>(base + off_step);
+  int* blk = step + 1;
 
   // spectral interval of H - s (needs the range of V: read back two doubles)
   double vmin = 0.0, vmax = 0.0;
   if (pb->V_dev) {
-    double* mm = partials;   // two doubles of scratch, rewritten by the passes later
-    minmax_kernel<<<1, 256, 0, stream>>>(pb->V_dev, n, mm);
+    minmax_kernel<<<1, 256, 0, stream>>>(pb->V_dev, n, partials);
     CUDA_TRY(cudaGetLastError());
     double h[2];
-    CUDA_TRY(cudaMemcpyAsync(h, mm, sizeof(h), cudaMemcpyDeviceToHost, stream));
+    CUDA_TRY(cudaMemcpyAsync(h, partials, sizeof(h), cudaMemcpyDeviceToHost, stream));
     CUDA_TRY(cudaStreamSynchronize(stream));
     if (!std::isfinite(h[0]) || !std::isfinite(h[1])) return fail(DIRAC_EINVAL, "V has non-finite entries");
     vmin = h[0];
     vmax = h[1];
   }
-  double pf = 1.0;
-  if (pb->stencil_order == 4) {
-    const double cs = 1.0 - std::sqrt(6.0) / 2.0;
-    pf = std::sqrt(1.0 - cs * cs) * (4.0 - cs) / 3.0;
-  }
-  const double px = pf / pb->dx + std::fabs(pb->A_x), py = pf / pb->dy + std::fabs(pb->A_y);
-  const double mc2 = pb->mass * pb->c * pb->c;
-  const double emax = std::sqrt(mc2 * mc2 + pb->c * pb->c * (px * px + py * py));
-  const double c0 = 0.5 * (vmin + vmax) - pb->energy_shift;
-  const double half = (emax + 0.5 * (vmax - vmin)) * (1.0 + 1e-8) + 1e-12;
-
-  PassParams p;
-  std::memset(&p, 0, sizeof(p));
-  s = noalloc_cheb(c0, half, dt, pb->energy_shift, p.cheb);
+  struct {
+    Problem pr;
+    ChebParams cheb;
+    FieldStep fs;
+  } host;   // on the stack; copied into the scratch
+  std::memset(&host, 0, sizeof(host));
+  double c0, half;
+  spectral_interval(pb->stencil_order, pb->dx, pb->dy, pb->mass, pb->c, std::fabs(pb->A_x),
+                    std::fabs(pb->A_y), vmin, vmax, pb->energy_shift, c0, half);
+  s = make_cheb(c0, half, dt, pb->energy_shift, host.cheb);
   if (s != DIRAC_OK) return s;
   const double kfac = (pb->stencil_order == 2) ? 2.0 : 12.0;
-  p.psi = psi;
-  p.V = pb->V_dev;
-  p.st = st;
-  p.partials = partials;
-  p.nx = nx;
-  p.ny = ny;
-  p.tiles_x = grid.x;
-  p.ntiles = grid.x * grid.y;
-  p.m = m;
-  p.kx = pb->c / (kfac * pb->dx);
-  p.ky = pb->c / (kfac * pb->dy);
-  p.mcc = mc2;
-  p.cAx = pb->c * pb->A_x;
-  p.cAy = pb->c * pb->A_y;
-  p.shift = pb->energy_shift;
-  p.dt = dt;
-  p.tol = tol;
-  p.kxf = (float)p.kx; p.kyf = (float)p.ky; p.cAxf = (float)p.cAx; p.cAyf = (float)p.cAy;
-  p.probe_coef = make_coef(1.0, 0.0, 0.0, p.mcc - p.shift, -p.mcc - p.shift);
+  const double mcc = pb->mass * pb->c * pb->c;
+  const int rblocks = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, RB_MAX));
+  Problem& d = host.pr;
+  d.nx = nx; d.ny = ny; d.tiles_x = tiles_x; d.tile_begin = 0; d.ntiles = ntiles;
+  d.rblk_begin = 0; d.rblk_count = rblocks;
+  d.psi = static_cast<vec4*>(psi_dev);
+  d.basis = base + off_basis;
+  d.ybuf0 = base + off_y;
+  d.ybuf1 = base + off_y + field;
+  d.V = pb->V_dev;
+  d.st = st;
+  d.partials = partials;
+  d.cheb = reinterpret_cast<const ChebParams*>(base + off_cheb);
+  d.kx = pb->c / (kfac * pb->dx);
+  d.ky = pb->c / (kfac * pb->dy);
+  d.kxf = (float)d.kx;
+  d.kyf = (float)d.ky;
+  d.shift = pb->energy_shift;
+  d.probe_coef = make_coef(1.0, 0.0, 0.0, mcc - pb->energy_shift, -mcc - pb->energy_shift);
+  host.fs.cAx = pb->c * pb->A_x;
+  host.fs.cAy = pb->c * pb->A_y;
+  host.fs.cAxf = (float)host.fs.cAx;
+  host.fs.cAyf = (float)host.fs.cAy;
+  CUDA_TRY(cudaMemcpyAsync(base, &host.pr, sizeof(Problem), cudaMemcpyHostToDevice, stream));
+  CUDA_TRY(cudaMemcpyAsync(base + off_cheb, &host.cheb, sizeof(ChebParams), cudaMemcpyHostToDevice, stream));
+  CUDA_TRY(cudaMemcpyAsync(base + off_field, &host.fs, sizeof(FieldStep), cudaMemcpyHostToDevice, stream));
+  // the scratch keeps the previous call's contents: restart the step counter,
+  // the block map (every block is problem 0) and the scalar block
+  CUDA_TRY(cudaMemsetAsync(step, 0, sizeof(int) * (1 + RB_MAX), stream));
+  CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(DevState), stream));
 
-  int n_sm = 0, dev = 0;
-  CUDA_TRY(cudaGetDevice(&dev));
-  CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
-  dirac_ctx view;   // launch configuration only; owns nothing
-  view.nx = nx; view.ny = ny; view.order = pb->stencil_order; view.boundary = pb->boundary;
-  view.has_v = pb->V_dev != nullptr; view.grid = grid; view.stream = stream;
-  view.precision = DIRAC_FP64; view.n_sm = n_sm;
-  p.pass = 1;
-  p.probe = 1;
-  CUDA_TRY(launch_pass(&view, p));
-  p.probe = 0;
-  for (int i = 1; i <= m; ++i) {
-    p.pass = i;
-    p.y_prev = (i >= 2) ? ybuf[(i - 1) & 1] : nullptr;
-    p.q_prev = (i == 2) ? (const void*)psi : (i >= 3 ? (const void*)(basis + (size_t)(i - 3) * n) : nullptr);
-    p.q_out = (i >= 2) ? (void*)(basis + (size_t)(i - 2) * n) : nullptr;
-    p.y_out = (i < m) ? (void*)ybuf[i & 1] : nullptr;
-    CUDA_TRY(launch_pass(&view, p));
+  LaunchParams lp;
+  std::memset(&lp, 0, sizeof(lp));
+  lp.probs = reinterpret_cast<const Problem*>(base);
+  lp.states = st;
+  lp.fields = reinterpret_cast<const FieldStep*>(base + off_field);
+  lp.fstride = 0;
+  lp.nprob = 1;
+  lp.total_tiles = ntiles;
+  lp.m = m;
+  lp.mcc = mcc;
+  lp.dt = dt;
+  lp.tol = tol;
+  lp.step = step;
+  lp.redo_budget = redo_budget(DIRAC_FP64, m);
+  lp.kappa_redo = kappa_redo(DIRAC_FP64);
+  LaunchShape ls{n_sm, 32, 0};
+  const bool diri = pb->boundary == DIRAC_DIRICHLET, hasv = pb->V_dev != nullptr;
+  lp.pass = 1;
+  lp.probe = 1;
+  CUDA_TRY(launch_pass(DIRAC_FP64, pb->stencil_order, diri, hasv, lp, ls, stream));
+  lp.probe = 0;
+  for (int i = 1; i <= m + lp.redo_budget; ++i) {
+    lp.pass = i;
+    CUDA_TRY(launch_pass(DIRAC_FP64, pb->stencil_order, diri, hasv, lp, ls, stream));
   }
-  const int rb = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, (long long)n_sm * 8));
-  CUDA_TRY(launch_pdl(recombine, rb, 256, stream, psi, (const vec4*)basis, n, st));
+  RecombParams rp;
+  rp.probs = lp.probs;
+  rp.blk_prob = blk;
+  rp.step = step;
+  rp.redo_budget = lp.redo_budget;
+  CUDA_TRY(launch_recombine(DIRAC_FP64, rp, rblocks, stream));
 
   if (info) {
     DevState h;

@@ -1,7 +1,9 @@
-// dirac_kernels.cuh -- device code of the GB300 Dirac Lanczos propagator (FP64 path).
+// dirac_kernels.cuh -- device code of the GB300 Dirac Lanczos propagator.
 //
 // One time step (Sec. 4, Eq. 17) is m launches of `lanczos_pass` (one Lanczos
-// iteration each, Fig. 1 / Eq. 4) and one launch of `recombine`.
+// iteration each, Fig. 1 / Eq. 4) and one launch of `recombine`.  Every launch
+// covers a table of independent problems (grids of any size); a single
+// propagation is a table of one.
 //
 // Pass i (1-based) works on unnormalised vectors whose scales are tracked by
 // device scalars:
@@ -19,8 +21,13 @@
 // The shift sigma_i = alpha_{i-1} keeps s2 free of cancellation (Y ~ s2),
 // and beta_{i-1} is taken from the measured norm of the next vector rather
 // than from s2, so the tridiagonal T of Fig. 1 is reproduced to rounding.
-// The last CTA of each pass sums the per-CTA partials in a fixed order
-// (deterministic, no floating-point atomics) and updates the scalars.
+//
+// Work split: the tiles of all problems form one list; persistent CTA c takes
+// the contiguous chunk [c T, (c+1) T).  Per problem it touches, a CTA writes
+// one partial (P, Y, X) into slot c - (first CTA of that problem) and adds
+// its tile count to the problem's ticket; the CTA that completes a problem
+// sums that problem's slots in a fixed order (deterministic, no
+// floating-point atomics) and updates its scalars.
 //
 // exp(-i T dt) e_1 (Sec. 4) is evaluated on one warp by a Chebyshev expansion
 // over an a-priori spectral interval of H (Jacobi-Anger coefficients computed
@@ -28,6 +35,10 @@
 // square root have latencies of several hundred cycles, which would make a
 // serial eigensolver dominate small steps, while the Chebyshev recurrence is
 // FMA-only and warp-parallel.  Both give exp(-i T dt) e_1 to rounding.
+//
+// Precision: S = double is the FP64 path.  S = float is the mixed path:
+// complex64 basis and y^, FP32 stencil, warp sums converted to FP64, FP64
+// scalars; q^_1 is the complex128 state itself (passes 1-2 read it).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -39,6 +50,8 @@ namespace dirac {
 constexpr int KMAX = 32;        // Krylov dimension limit (one warp holds T)
 constexpr int CHEB_MAX = 160;   // Chebyshev terms limit
 constexpr int ERR_NONFINITE = 4;
+constexpr int TILE_W = 32;      // tile width in sites (one warp)
+constexpr int RPT = 4;          // rows per thread
 
 using vec4 = double4_32a;       // one site: (u.re, u.im, d.re, d.im)
 
@@ -63,22 +76,21 @@ __host__ __device__ inline PassCoef make_coef(double g, double gd, double e, dou
 }
 
 struct DevState {
-  PassCoef pc[KMAX + 2];    // coefficients of pass i (pc[1]: first pass of a step)
+  PassCoef pc_cur;          // coefficients of the next pass to run
+  int cur_pass;             // the next pass to run (1-based; 0 reads as 1)
+  int redo_left;            // re-runs of a pass still allowed in this step
   double alpha[KMAX + 2];   // T diagonal of H - s, index 1..k
   double beta[KMAX + 2];    // beta[i] couples i and i+1; beta[k] = beta_k estimate
   double nu[KMAX + 2];      // ||q^_i||
   double inv_nu[KMAX + 2];  // 1 / ||q^_i||
   double sigma[KMAX + 2];   // stencil shift of pass i
-  double g[KMAX + 2];
-  double d[KMAX + 2];
-  double e[KMAX + 2];
   double coef_re[KMAX + 2]; // recombination coefficients C_j, j = 1..k
   double coef_im[KMAX + 2];
   double scale;             // running max(|alpha_j + s|, beta_j) for breakdown
   double psi_norm, energy, err_est, cum_err, beta_last, kappa_max;
   int stopped;              // passes of this step are done (or an error is pending)
   int k_used, breakdown, error, sigma_valid;
-  unsigned counter;         // last-CTA ticket of the running pass
+  unsigned counter;         // tiles of the running pass completed so far
 };
 
 struct ChebParams {
@@ -90,29 +102,54 @@ struct ChebParams {
   double ci[CHEB_MAX];      //                               imaginary part
 };
 
-struct PassParams {
-  const void* psi;          // q^_1 (the FP64 state, read in place)
-  const void* y_prev;       // y^_{i-1}
-  const void* q_prev;       // q^_{i-1}
-  void* q_out;              // q^_i  (i >= 2)
-  void* y_out;              // y^_i  (NULL on the last pass)
-  const void* V;            // potential energy [ny][nx] (double) or NULL
+// c * A of one step (electron: p - qA = p + A), FP64 and FP32
+struct FieldStep {
+  double cAx, cAy;
+  float cAxf, cAyf, pad0, pad1;
+};
+
+// One independent propagation problem.
+struct Problem {
+  int nx, ny, tiles_x, tile_begin, ntiles;   // tiles of TILE_W x TH sites
+  int rblk_begin, rblk_count;                // recombination blocks
+  const vec4* psi;          // the state (complex128), q^_1
+  void* basis;              // q^_2 .. q^_m
+  void* ybuf0;              // y^ ping-pong
+  void* ybuf1;
+  const void* V;            // potential energy in S, or NULL
   DevState* st;
-  double* partials;         // 3 doubles per CTA
-  int nx, ny;
-  int tiles_x, ntiles;      // tiles of TILE x TILE sites (grid-stride over them)
+  double* partials;         // 3 doubles per slot
+  const ChebParams* cheb;
+  double kx, ky, shift;     // c/(2dx) (order 2) or c/(12dx) (order 4); energy shift
+  float kxf, kyf;
+  PassCoef probe_coef;      // coefficients of the probe pass (stencil shift 0)
+};
+
+struct LaunchParams {
+  const Problem* probs;
+  int redo_budget;          // re-runs allowed per step (the spare launches)
+  double kappa_redo;        // re-run a pass whose ||y^||^2 / s2 exceeds this
+  DevState* states;         // one per problem, same order
+  const FieldStep* fields;  // fields[step * fstride + problem]
+  int fstride;              // 0: one FieldStep per problem for every step
+  int nprob, total_tiles, tiles_per_cta;
   int pass, m, probe;
-  double kx, ky;            // c/(2dx) (order 2) or c/(12dx) (order 4)
-  double mcc, cAx, cAy, shift, dt, tol;
-  float kxf, kyf, cAxf, cAyf; // the same four in FP32 (rounded on the host)
-  PassCoef probe_coef;      // coefficients of the probe pass (shift 0)
-  ChebParams cheb;
+  double mcc, dt, tol;
+  const int* step;          // step counter of the running call (index into fields)
+};
+
+struct RecombParams {
+  const Problem* probs;
+  const int* blk_prob;      // problem of each block
+  int* step;                // advanced once per step
+  int redo_budget;
 };
 
 // ---------------------------------------------------------------------------
 // small helpers
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double warp_sum(double v) {
+template <class S>
+__device__ __forceinline__ S warp_sum(S v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -128,9 +165,17 @@ __device__ __forceinline__ int wrap(int g, int n, bool& outside) {
   return r < 0 ? r + n : r;
 }
 
+template <class S> struct Vec4;
+template <> struct Vec4<double> { using T = double4_32a; };
+template <> struct Vec4<float> { using T = float4; };
+
+template <class To, class From>
+__device__ __forceinline__ void cvt4(const From& a, To (&o)[4]) {
+  o[0] = (To)a.x; o[1] = (To)a.y; o[2] = (To)a.z; o[3] = (To)a.w;
+}
+
 // ---------------------------------------------------------------------------
 // exp(-i T dt) e_1 on one warp: lane j holds component j+1 (k <= 32).
-// T diagonal alpha[1..k], off-diagonal beta[1..k-1] (1-based arrays).
 // X = (T - c0) / half has its spectrum in [-1, 1]; exp(-i R X) with
 // R = half * dt is sum_n eps_n (-i)^n J_n(R) T_n(X) (Jacobi-Anger), summed
 // with the three-term Chebyshev recurrence T_{n+1} = 2 X T_n - T_{n-1}.
@@ -167,23 +212,26 @@ __device__ void cheb_expm_e1(const ChebParams& cp, int k, double alpha_j, double
 }
 
 // ---------------------------------------------------------------------------
-// Scalar update after pass i: run by warp 0 of the last CTA with the grid
+// Scalar update of one problem after pass i: run by one warp with the grid
 // totals P, Y, X in every lane.  Values written by earlier launches are read
 // with plain loads up front; new values travel by shuffles.  rsqrt gives
 // sqrt(X), 1/X, sqrt(s2) and 1/sqrt(s2) with few dependent FP64 operations.
 // ---------------------------------------------------------------------------
-__device__ void finish_pass(const PassParams& p, double P, double Y, double X) {
-  DevState* st = p.st;
+__device__ void finish_pass(const LaunchParams& lp, const Problem* pr, int i, double P, double Y,
+                            double X) {
+  DevState* st = pr->st;
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const int i = p.pass;
+  const double shift = pr->shift;
   const bool ok = isfinite(P) && isfinite(Y) && isfinite(X) && X > 0.0;
-  if (p.probe) {   // Rayleigh quotient of psi: the first stencil shift
+  if (lp.probe) {   // Rayleigh quotient of psi: the first stencil shift
     if (lane == 0) {
       if (ok) {
-        const double s1 = P / X;   // the probe ran with shift 0
+        const double s1 = P / X;   // the probe ran with stencil shift 0
         st->sigma[1] = s1;
-        st->pc[1] = make_coef(1.0, 0.0, 0.0, p.mcc - p.shift - s1, -p.mcc - p.shift - s1);
+        st->pc_cur = make_coef(1.0, 0.0, 0.0, lp.mcc - shift - s1, -lp.mcc - shift - s1);
+        st->cur_pass = 1;
+        st->redo_left = lp.redo_budget;
         st->sigma_valid = 1;
       } else {
         st->error = ERR_NONFINITE; st->stopped = 1;
@@ -203,7 +251,10 @@ __device__ void finish_pass(const PassParams& p, double P, double Y, double X) {
   const double scale_old = (i == 1) ? 0.0 : st->scale;
   const double bhat_prev = (i == 1) ? 0.0 : st->beta[i - 1];       // estimate from pass i-1
   const double nu1_old = (i == 1) ? 0.0 : st->nu[1];
+  const double alpha1_old = (i == 1) ? 0.0 : st->alpha[1];
   const double psi_norm_old = st->psi_norm, cum_old = st->cum_err;
+  const int redo_left = st->redo_left;
+  const PassCoef pc_now = st->pc_cur;
 
   // scalar chain (every lane computes it; no broadcast needed)
   const double y = rsqrt(X);            // 1 / nu_i
@@ -216,27 +267,39 @@ __device__ void finish_pass(const PassParams& p, double P, double Y, double X) {
   const double sq = s2 > 0.0 ? s2 * rs : 0.0;
   const double beta_hat = sq * y;
   const double bprev = nu * bhat_prev;  // exact beta_{i-1} from the measured norm
-  double scale = fmax(scale_old, fabs(alpha + p.shift));
+  // The stencil shift sigma_i was too far from alpha_i for the precision of
+  // y^ (s2 is then cancellation noise): run pass i again with sigma_i =
+  // alpha_i, which makes s2 ~ Y.  Everything derived from X (nu, beta_{i-1})
+  // is unchanged by the re-run.
+  if ((!(s2 > 0.0) || Y > lp.kappa_redo * s2) && redo_left > 0) {
+    if (lane == 0) {
+      st->redo_left = redo_left - 1;
+      st->sigma[i] = alpha;
+      st->pc_cur = make_coef(pc_now.g, pc_now.gd, pc_now.e, lp.mcc - shift - alpha,
+                             -lp.mcc - shift - alpha);
+      if (s2 > 0.0) st->kappa_max = fmax(st->kappa_max, Y * rs * rs);
+    }
+    return;
+  }
+  double scale = fmax(scale_old, fabs(alpha + shift));
   if (i > 1) scale = fmax(scale, bprev);
   const int brk = beta_hat <= 1e-12 * scale;
-  int stop = (i >= p.m) || brk;
+  int stop = (i >= lp.m) || brk;
   const double nu1 = (i == 1) ? nu : nu1_old;
   const double psi_norm = (i == 1) ? nu : psi_norm_old;
   if (lane == 0) {
     st->nu[i] = nu;
     st->inv_nu[i] = y;
     st->alpha[i] = alpha;
-    st->d[i] = dd;
     st->beta[i] = beta_hat;
     if (i > 1) st->beta[i - 1] = bprev;
     st->scale = scale;
-    if (i == 1) { st->psi_norm = nu; st->energy = alpha + p.shift; }
+    if (i == 1) { st->psi_norm = nu; st->energy = alpha + shift; }
     if (s2 > 0.0) st->kappa_max = fmax(st->kappa_max, Y * rs * rs);
     if (!stop) {
-      st->g[i] = rs;
-      st->e[i + 1] = sq * rX;
       st->sigma[i + 1] = alpha;
-      st->pc[i + 1] = make_coef(rs, rs * dd, sq * rX, p.mcc - p.shift - alpha, -p.mcc - p.shift - alpha);
+      st->pc_cur = make_coef(rs, rs * dd, sq * rX, lp.mcc - shift - alpha, -lp.mcc - shift - alpha);
+      st->cur_pass = i + 1;
     }
   }
   // this lane's row of T^(i)
@@ -246,14 +309,14 @@ __device__ void finish_pass(const PassParams& p, double P, double Y, double X) {
   const double inv_nu_j = (lane + 1 == i) ? y : invnu_old;
   double vr = 0.0, vi = 0.0;
   bool have_v = false;
-  if (!stop && p.tol > 0.0) {   // adaptive Krylov dimension (Sec. 4, Eq. 18)
-    cheb_expm_e1(p.cheb, i, a_j, b_lo, b_hi, vr, vi);
+  if (!stop && lp.tol > 0.0) {   // adaptive Krylov dimension (Sec. 4, Eq. 18)
+    cheb_expm_e1(*pr->cheb, i, a_j, b_lo, b_hi, vr, vi);
     have_v = true;
     const double vk = __shfl_sync(full, sqrt(vr * vr + vi * vi), i - 1);
-    stop = (beta_hat * p.dt * vk <= p.tol);
+    stop = (beta_hat * lp.dt * vk <= lp.tol);
   }
   if (!stop) return;
-  if (!have_v) cheb_expm_e1(p.cheb, i, a_j, b_lo, b_hi, vr, vi);
+  if (!have_v) cheb_expm_e1(*pr->cheb, i, a_j, b_lo, b_hi, vr, vi);
   // C_j = nu_1 / nu_j * v_j applied to q^_j; Eq. 18 estimate from v_k
   const double vk = __shfl_sync(full, sqrt(vr * vr + vi * vi), i - 1);
   if (lane < i) {
@@ -262,319 +325,354 @@ __device__ void finish_pass(const PassParams& p, double P, double Y, double X) {
     st->coef_im[lane + 1] = f * vi;
   }
   if (lane == 0) {
-    const double err = p.dt * beta_hat * psi_norm * vk;
+    const double err = lp.dt * beta_hat * psi_norm * vk;
     st->err_est = err;
     st->cum_err = cum_old + err;
     st->k_used = i;
     st->breakdown = brk;
     st->beta_last = beta_hat;
-    const double s1 = (i == 1) ? alpha : st->alpha[1];   // next step's first shift
+    const double s1 = (i == 1) ? alpha : alpha1_old;   // next step's first shift
     st->sigma[1] = s1;
-    st->pc[1] = make_coef(1.0, 0.0, 0.0, p.mcc - p.shift - s1, -p.mcc - p.shift - s1);
+    st->pc_cur = make_coef(1.0, 0.0, 0.0, lp.mcc - shift - s1, -lp.mcc - shift - s1);
     st->sigma_valid = 1;
     st->stopped = 1;
   }
 }
 
 // ---------------------------------------------------------------------------
-// One Lanczos iteration: stencil product with fused reductions.
+// One Lanczos iteration over every problem of the table: stencil product
+// with fused reductions.
 //
 // S    arithmetic type of the stencil (double: FP64 path; float: mixed path)
 // R    stencil half width (1: order 2, 2: order 4)
-// QIN64  q^_{i-1} (and psi) are complex128 (FP64 path, and passes 1-2 of the
-//      mixed path, whose q^_1 is the FP64 state itself); otherwise they are
-//      stored like y^ (complex64 in the mixed path)
+// TH   tile height in sites (tiles are TILE_W x TH; TH / RPT warps per CTA)
 //
-// A CTA owns a TILE x TILE block of sites; thread (tx, tg) handles column tx
-// and rows tg, tg + NG, tg + 2 NG, tg + 3 NG (NG = TILE / RPT), so every warp
-// touches one contiguous row segment per access.  The tile and a cross-shaped
-// halo of q^_i are formed in shared memory from y^_{i-1} and q^_{i-1}.
+// Each problem runs its own next pass (DevState::cur_pass), so that a pass
+// can be re-run (see finish_pass) without the host knowing.  q^_{i-1} (and
+// psi) are complex128 on the FP64 path and in passes 1-2 of the mixed path
+// (whose q^_1 is the FP64 state itself), else complex64.
+//
+// Thread (tx, tg) handles column tx and rows tg, tg + NG, ..., so every warp
+// touches one contiguous row segment per access.  The tile and a
+// cross-shaped halo of q^_i are formed in shared memory from y^_{i-1} and
+// q^_{i-1}.
 // ---------------------------------------------------------------------------
-template <class S> struct Vec4;
-template <> struct Vec4<double> { using T = double4_32a; };
-template <> struct Vec4<float> { using T = float4; };
+template <class S, int TH>
+constexpr int min_blocks() { return sizeof(S) == sizeof(float) ? (TH == 32 ? 4 : 8) : 2; }
 
-template <class To, class From>
-__device__ __forceinline__ void cvt4(const From& a, To (&o)[4]) {
-  o[0] = (To)a.x; o[1] = (To)a.y; o[2] = (To)a.z; o[3] = (To)a.w;
-}
-
-template <class S>
-__device__ __forceinline__ S warp_sum_t(S v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-constexpr int TILE = 32;          // tile edge (sites)
-constexpr int RPT = 4;            // rows per thread
-constexpr int NG = TILE / RPT;    // row groups
-constexpr int NTP = 32 * NG;      // threads per CTA (256)
-
-template <class S, int R, bool DIRI, bool HAS_V, bool QIN64>
-__global__ void __launch_bounds__(NTP, sizeof(S) == sizeof(float) ? 5 : 2)
-lanczos_pass(const __grid_constant__ PassParams p) {
-  using T4 = typename Vec4<S>::T;           // storage of y^ and (if !QIN64) q^
-  constexpr int W = TILE + 2 * R;
-  __shared__ __align__(32) S tile[TILE + 2 * R][W][4];
-  __shared__ double red[NTP / 32][3];
-  __shared__ int last_cta;
-  // programmatic dependent launch: everything above may overlap the tail of
-  // the previous kernel; nothing it wrote is read before this point
+template <class S, int R, int TH, bool DIRI, bool HAS_V>
+__global__ void __launch_bounds__(32 * (TH / RPT), (min_blocks<S, TH>()))
+lanczos_pass(const __grid_constant__ LaunchParams lp) {
+  using T4 = typename Vec4<S>::T;           // storage of y^ (and of q^ on the mixed path)
+  constexpr int NG = TH / RPT;              // row groups = warps
+  constexpr int NT = 32 * NG;               // threads
+  constexpr int W = TILE_W + 2 * R;
+  __shared__ __align__(32) S tile[TH + 2 * R][W][4];
+  __shared__ double red[NG][3];
+  __shared__ int last_flag;
+  // programmatic dependent launch: nothing the previous kernel wrote is read
+  // before this point
   asm volatile("griddepcontrol.wait;" ::: "memory");
-  const DevState* st = p.st;   // written by earlier launches: plain loads
-  if (st->stopped) return;
-  const int i = p.pass;
-  const PassCoef pc = p.probe ? p.probe_coef : st->pc[i];
-  constexpr bool F32 = sizeof(S) == sizeof(float);
-  const S gS = F32 ? (S)pc.gf : (S)pc.g;
-  const S gdS = F32 ? (S)pc.gdf : (S)pc.gd;
-  const S eS = F32 ? (S)pc.ef : (S)pc.e;
-  const int nx = p.nx, ny = p.ny;
+
+  const int t_begin = blockIdx.x * lp.tiles_per_cta;
+  const int t_end = min(t_begin + lp.tiles_per_cta, lp.total_tiles);
   const int tx = threadIdx.x & 31, tg = threadIdx.x >> 5;
-  const T4* yprev = static_cast<const T4*>(p.y_prev);
-  const S kx = F32 ? (S)p.kxf : (S)p.kx, ky = F32 ? (S)p.kyf : (S)p.ky;
-  const S cAx = F32 ? (S)p.cAxf : (S)p.cAx, cAy = F32 ? (S)p.cAyf : (S)p.cAy;
-  const S au_hi = F32 ? (S)pc.au_hi : (S)pc.au0, au_lo = F32 ? (S)pc.au_lo : S(0);
-  const S ad_hi = F32 ? (S)pc.ad_hi : (S)pc.ad0, ad_lo = F32 ? (S)pc.ad_lo : S(0);
-  S accP = S(0), accY = S(0), accX = S(0);
-  int x0 = 0, y0 = 0;
+  const int warp = tg, lane = tx;
+  const int step = *lp.step;
+  constexpr bool F32 = sizeof(S) == sizeof(float);
 
-  // q^_i at grid point (gx, gy) (zero outside for Dirichlet) into smem slot
-  auto form = [&](int gx, int gy, int row, int col, S (&qp)[4]) {
-    bool ox, oy;
-    const int ix = wrap<DIRI>(gx, nx, ox), iy = wrap<DIRI>(gy, ny, oy);
-    S q[4] = {S(0), S(0), S(0), S(0)};
-    qp[0] = qp[1] = qp[2] = qp[3] = S(0);
-    if (!(ox || oy)) {
-      const size_t idx = (size_t)iy * nx + ix;
-      if constexpr (QIN64) {
-        const double4_32a* qsrc = static_cast<const double4_32a*>(i == 1 ? p.psi : p.q_prev);
-        cvt4(qsrc[idx], qp);
-      } else {
-        cvt4(static_cast<const T4*>(p.q_prev)[idx], qp);
-      }
-      if (i == 1) {
-#pragma unroll
-        for (int c = 0; c < 4; ++c) q[c] = qp[c];
-      } else {
-        S yv[4];
-        cvt4(yprev[idx], yv);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) q[c] = fma(-gdS, qp[c], gS * yv[c]);
-      }
+  // problem of the first tile (problems are sorted by tile_begin)
+  int b = 0;
+  {
+    int lo = 0, hi = lp.nprob - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (lp.probs[mid].tile_begin <= t_begin) lo = mid; else hi = mid - 1;
     }
-#pragma unroll
-    for (int c = 0; c < 4; ++c) tile[row][col][c] = q[c];
-  };
-
-  for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
-  x0 = (t % p.tiles_x) * TILE;
-  y0 = (t / p.tiles_x) * TILE;
-  S qprev[RPT][4];
-#pragma unroll
-  for (int k = 0; k < RPT; ++k) {
-    const int r = tg + k * NG;
-    form(x0 + tx, y0 + r, r + R, tx + R, qprev[k]);
+    b = lo;
   }
-  constexpr int NH_ROW = 2 * R * TILE, NH = 2 * NH_ROW;
-  for (int h = threadIdx.x; h < NH; h += NTP) {
-    int row, col;
-    if (h < NH_ROW) {               // rows above / below
-      const int r = h / TILE;
-      row = (r < R) ? r : TILE + r;
-      col = (h % TILE) + R;
-    } else {                        // columns left / right
-      const int h2 = h - NH_ROW;
-      row = h2 / (2 * R) + R;
-      const int c = h2 % (2 * R);
-      col = (c < R) ? c : TILE + c;
-    }
-    S dummy[4];
-    form(x0 + col - R, y0 + row - R, row, col, dummy);
-  }
-  __syncthreads();
+  for (int t = t_begin; t < t_end; ++b) {
+    const Problem* pr = lp.probs + b;
+    const DevState* st = lp.states + b;
+    // independent loads first (all addresses are valid), then the branch
+    const int stopped = st->stopped;
+    const int i = lp.probe ? 1 : max(1, st->cur_pass);
+    const PassCoef pc = lp.probe ? pr->probe_coef : st->pc_cur;
+    const FieldStep fs = lp.fields[step * lp.fstride + b];
+    const int seg_end = min(t_end, pr->tile_begin + pr->ntiles);
+    const int seg_tiles = seg_end - t;
+    if (stopped) { t = seg_end; continue; }
+    const S gS = F32 ? (S)pc.gf : (S)pc.g;
+    const S gdS = F32 ? (S)pc.gdf : (S)pc.gd;
+    const S eS = F32 ? (S)pc.ef : (S)pc.e;
+    const S kx = F32 ? (S)pr->kxf : (S)pr->kx, ky = F32 ? (S)pr->kyf : (S)pr->ky;
+    const S cAx = F32 ? (S)fs.cAxf : (S)fs.cAx, cAy = F32 ? (S)fs.cAyf : (S)fs.cAy;
+    const S au_hi = F32 ? (S)pc.au_hi : (S)pc.au0, au_lo = F32 ? (S)pc.au_lo : S(0);
+    const S ad_hi = F32 ? (S)pc.ad_hi : (S)pc.ad0, ad_lo = F32 ? (S)pc.ad_lo : S(0);
+    const int nx = pr->nx, ny = pr->ny;
+    const size_t n = (size_t)nx * ny;
+    // this pass's vectors
+    constexpr int SB = F32 ? (int)sizeof(float4) : (int)sizeof(double4_32a);
+    const char* basis = static_cast<const char*>(pr->basis);
+    const void* y_prev = (i >= 2) ? (((i - 1) & 1) ? pr->ybuf1 : pr->ybuf0) : nullptr;
+    const void* q_prev = (i == 2) ? (const void*)pr->psi
+                                  : (i >= 3 ? (const void*)(basis + (size_t)(i - 3) * n * SB) : nullptr);
+    void* q_out = (i >= 2) ? (void*)(basis + (size_t)(i - 2) * n * SB) : nullptr;
+    void* y_out = (i < lp.m) ? ((i & 1) ? pr->ybuf1 : pr->ybuf0) : nullptr;
+    const T4* yprev = static_cast<const T4*>(y_prev);
+    const bool q64 = !F32 || i <= 2;                // q^_{i-1} stored as complex128
+    const S* Vp = static_cast<const S*>(pr->V);   // NULL: V = 0 for this problem
 
-#pragma unroll
-  for (int k = 0; k < RPT; ++k) {
-    const int ry = tg + k * NG;
-    const int x = x0 + tx, y = y0 + ry;
-    if (x < nx && y < ny) {
-      const size_t idx = (size_t)y * nx + x;
-      const int r = ry + R, c = tx + R;
-      S C[4], dxv[4], dyv[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        C[q] = tile[r][c][q];
-        dxv[q] = tile[r][c + 1][q] - tile[r][c - 1][q];
-        dyv[q] = tile[r + 1][c][q] - tile[r - 1][c][q];
-        if constexpr (R == 2) {
-          dxv[q] = fma(S(8), dxv[q], tile[r][c - 2][q] - tile[r][c + 2][q]);
-          dyv[q] = fma(S(8), dyv[q], tile[r - 2][c][q] - tile[r + 2][c][q]);
+    // q^_i at grid point (gx, gy) (zero outside for Dirichlet) into smem slot
+    auto form = [&](int gx, int gy, int row, int col, S (&qp)[4]) {
+      bool ox, oy;
+      const int ix = wrap<DIRI>(gx, nx, ox), iy = wrap<DIRI>(gy, ny, oy);
+      S q[4] = {S(0), S(0), S(0), S(0)};
+      qp[0] = qp[1] = qp[2] = qp[3] = S(0);
+      if (!(ox || oy)) {
+        const size_t idx = (size_t)iy * nx + ix;
+        if (q64) {
+          const vec4* qsrc = (i == 1) ? pr->psi : static_cast<const vec4*>(q_prev);
+          cvt4(qsrc[idx], qp);
+        } else {
+          cvt4(static_cast<const float4*>(q_prev)[idx], qp);
         }
-      }
-      S au, ad;
-      if constexpr (HAS_V) {       // V stored in S (float copy on the mixed path)
-        const S v = static_cast<const S*>(p.V)[idx];
-        au = au_hi + v;
-        ad = ad_hi + v;
-      } else {
-        au = au_hi;
-        ad = ad_hi;
-      }
-      // C = (u.re, u.im, d.re, d.im); dxv/dyv likewise
-      S yv[4];
-      // upper: (mc^2+V-s-sigma) u + c[-i D_x d - D_y d + (A_x - i A_y) d]
-      yv[0] = au * C[0] + kx * dxv[3] - ky * dyv[2] + cAx * C[2] + cAy * C[3];
-      yv[1] = au * C[1] - kx * dxv[2] - ky * dyv[3] + cAx * C[3] - cAy * C[2];
-      // lower: (-mc^2+V-s-sigma) d + c[-i D_x u + D_y u + (A_x + i A_y) u]
-      yv[2] = ad * C[2] + kx * dxv[1] + ky * dyv[0] + cAx * C[0] - cAy * C[1];
-      yv[3] = ad * C[3] - kx * dxv[0] + ky * dyv[1] + cAx * C[1] + cAy * C[0];
-      if constexpr (sizeof(S) == sizeof(float)) {
-        yv[0] = fma(au_lo, C[0], yv[0]);
-        yv[1] = fma(au_lo, C[1], yv[1]);
-        yv[2] = fma(ad_lo, C[2], yv[2]);
-        yv[3] = fma(ad_lo, C[3], yv[3]);
-      }
-      if (i >= 2) {
+        if (i == 1) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) yv[q] = fma(-eS, qprev[k][q], yv[q]);
-      }
-      if (!p.probe) {
-        if (p.q_out) {
-          T4 o; o.x = C[0]; o.y = C[1]; o.z = C[2]; o.w = C[3];
-          static_cast<T4*>(p.q_out)[idx] = o;
-        }
-        if (p.y_out) {
-          T4 o; o.x = yv[0]; o.y = yv[1]; o.z = yv[2]; o.w = yv[3];
-          static_cast<T4*>(p.y_out)[idx] = o;
+          for (int c = 0; c < 4; ++c) q[c] = qp[c];
+        } else {
+          S yv[4];
+          cvt4(yprev[idx], yv);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) q[c] = fma(-gdS, qp[c], gS * yv[c]);
         }
       }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        accP = fma(C[q], yv[q], accP);
-        accY = fma(yv[q], yv[q], accY);
-        accX = fma(C[q], C[q], accX);
+      for (int c = 0; c < 4; ++c) tile[row][col][c] = q[c];
+    };
+
+    S accP = S(0), accY = S(0), accX = S(0);
+    for (; t < seg_end; ++t) {
+      const int lt = t - pr->tile_begin;
+      const int x0 = (lt % pr->tiles_x) * TILE_W;
+      const int y0 = (lt / pr->tiles_x) * TH;
+      S qprev[RPT][4];
+#pragma unroll
+      for (int k = 0; k < RPT; ++k) {
+        const int r = tg + k * NG;
+        form(x0 + tx, y0 + r, r + R, tx + R, qprev[k]);
+      }
+      constexpr int NH_ROW = 2 * R * TILE_W, NH = NH_ROW + 2 * R * TH;
+      for (int h = threadIdx.x; h < NH; h += NT) {
+        int row, col;
+        if (h < NH_ROW) {               // rows above / below
+          const int r = h / TILE_W;
+          row = (r < R) ? r : TH + r;
+          col = (h % TILE_W) + R;
+        } else {                        // columns left / right
+          const int h2 = h - NH_ROW;
+          row = h2 / (2 * R) + R;
+          const int c = h2 % (2 * R);
+          col = (c < R) ? c : TILE_W + c;
+        }
+        S dummy[4];
+        form(x0 + col - R, y0 + row - R, row, col, dummy);
+      }
+      __syncthreads();
+
+#pragma unroll
+      for (int k = 0; k < RPT; ++k) {
+        const int ry = tg + k * NG;
+        const int x = x0 + tx, y = y0 + ry;
+        if (x < nx && y < ny) {
+          const size_t idx = (size_t)y * nx + x;
+          const int r = ry + R, c = tx + R;
+          S C[4], dxv[4], dyv[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            C[q] = tile[r][c][q];
+            dxv[q] = tile[r][c + 1][q] - tile[r][c - 1][q];
+            dyv[q] = tile[r + 1][c][q] - tile[r - 1][c][q];
+            if constexpr (R == 2) {
+              dxv[q] = fma(S(8), dxv[q], tile[r][c - 2][q] - tile[r][c + 2][q]);
+              dyv[q] = fma(S(8), dyv[q], tile[r - 2][c][q] - tile[r + 2][c][q]);
+            }
+          }
+          S au, ad;
+          if (HAS_V && Vp != nullptr) {   // V stored in S (float copy on the mixed path)
+            const S v = Vp[idx];
+            au = au_hi + v;
+            ad = ad_hi + v;
+          } else {
+            au = au_hi;
+            ad = ad_hi;
+          }
+          // C = (u.re, u.im, d.re, d.im); dxv/dyv likewise
+          S yv[4];
+          // upper: (mc^2+V-s-sigma) u + c[-i D_x d - D_y d + (A_x - i A_y) d]
+          yv[0] = au * C[0] + kx * dxv[3] - ky * dyv[2] + cAx * C[2] + cAy * C[3];
+          yv[1] = au * C[1] - kx * dxv[2] - ky * dyv[3] + cAx * C[3] - cAy * C[2];
+          // lower: (-mc^2+V-s-sigma) d + c[-i D_x u + D_y u + (A_x + i A_y) u]
+          yv[2] = ad * C[2] + kx * dxv[1] + ky * dyv[0] + cAx * C[0] - cAy * C[1];
+          yv[3] = ad * C[3] - kx * dxv[0] + ky * dyv[1] + cAx * C[1] + cAy * C[0];
+          if constexpr (F32) {
+            yv[0] = fma(au_lo, C[0], yv[0]);
+            yv[1] = fma(au_lo, C[1], yv[1]);
+            yv[2] = fma(ad_lo, C[2], yv[2]);
+            yv[3] = fma(ad_lo, C[3], yv[3]);
+          }
+          if (i >= 2) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) yv[q] = fma(-eS, qprev[k][q], yv[q]);
+          }
+          if (!lp.probe) {
+            if (q_out) {
+              T4 o; o.x = C[0]; o.y = C[1]; o.z = C[2]; o.w = C[3];
+              static_cast<T4*>(q_out)[idx] = o;
+            }
+            if (y_out) {
+              T4 o; o.x = yv[0]; o.y = yv[1]; o.z = yv[2]; o.w = yv[3];
+              static_cast<T4*>(y_out)[idx] = o;
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            accP = fma(C[q], yv[q], accP);
+            accY = fma(yv[q], yv[q], accY);
+            accX = fma(C[q], C[q], accX);
+          }
+        }
+      }
+      __syncthreads();   // the tile buffer is reused next
+    }
+
+    // this CTA's share of the problem: thread -> warp in S, warps -> CTA in
+    // double, one partial per (problem, CTA) slot, then the ticket
+    accP = warp_sum(accP);
+    accY = warp_sum(accY);
+    accX = warp_sum(accX);
+    if (lane == 0) { red[warp][0] = (double)accP; red[warp][1] = (double)accY; red[warp][2] = (double)accX; }
+    __syncthreads();
+    if (warp == 0) {
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+      if (lane < NG) { s0 = red[lane][0]; s1 = red[lane][1]; s2 = red[lane][2]; }
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) {   // NG <= 8 warps
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+      }
+      if (lane == 0) {
+        const int slot = blockIdx.x - pr->tile_begin / lp.tiles_per_cta;
+        pr->partials[3 * slot + 0] = s0;
+        pr->partials[3 * slot + 1] = s1;
+        pr->partials[3 * slot + 2] = s2;
+        // release our partial / acquire everybody else's
+        cuda::atomic_ref<unsigned, cuda::thread_scope_device> ticket(pr->st->counter);
+        last_flag = (ticket.fetch_add((unsigned)seg_tiles, cuda::memory_order_acq_rel) + seg_tiles ==
+                     (unsigned)pr->ntiles);
       }
     }
+    __syncthreads();
+    if (last_flag && warp == 0) {
+      // the problem is complete: sum its slots in a fixed order
+      const int cta_lo = pr->tile_begin / lp.tiles_per_cta;
+      const int nslots = (pr->tile_begin + pr->ntiles - 1) / lp.tiles_per_cta - cta_lo + 1;
+      double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+      for (int s = lane; s < nslots; s += 32) {
+        t0 += __ldcg(pr->partials + 3 * s + 0);
+        t1 += __ldcg(pr->partials + 3 * s + 1);
+        t2 += __ldcg(pr->partials + 3 * s + 2);
+      }
+      t0 = warp_sum(t0);
+      t1 = warp_sum(t1);
+      t2 = warp_sum(t2);
+      if (lane == 0) pr->st->counter = 0u;
+      finish_pass(lp, pr, i, t0, t1, t2);
+    }
+    __syncthreads();
   }
-  __syncthreads();   // the tile is reused by the next iteration
-  }
-
   // the next kernel may be scheduled now (it waits for our completion)
   asm volatile("griddepcontrol.launch_dependents;");
-  // reductions: thread -> warp in S, warp -> CTA in double (fixed order)
-  accP = warp_sum_t(accP);
-  accY = warp_sum_t(accY);
-  accX = warp_sum_t(accX);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) { red[warp][0] = (double)accP; red[warp][1] = (double)accY; red[warp][2] = (double)accX; }
-  __syncthreads();
-  const unsigned ncta = gridDim.x;
-  const unsigned cta = blockIdx.x;
-  if (threadIdx.x == 0) {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-#pragma unroll
-    for (int w = 0; w < NTP / 32; ++w) { s0 += red[w][0]; s1 += red[w][1]; s2 += red[w][2]; }
-    p.partials[3 * (size_t)cta + 0] = s0;
-    p.partials[3 * (size_t)cta + 1] = s1;
-    p.partials[3 * (size_t)cta + 2] = s2;
-    // release our partials / acquire everybody else's
-    cuda::atomic_ref<unsigned, cuda::thread_scope_device> ticket(p.st->counter);
-    last_cta = (ticket.fetch_add(1u, cuda::memory_order_acq_rel) == ncta - 1);
-  }
-  __syncthreads();
-  if (!last_cta || warp != 0) return;
-
-  // last CTA, warp 0: sum all partials in a fixed order
-  double t0 = 0.0, t1 = 0.0, t2 = 0.0;
-  for (unsigned b = lane; b < ncta; b += 32) {
-    t0 += __ldcg(p.partials + 3 * (size_t)b + 0);
-    t1 += __ldcg(p.partials + 3 * (size_t)b + 1);
-    t2 += __ldcg(p.partials + 3 * (size_t)b + 2);
-  }
-  t0 = warp_sum(t0);
-  t1 = warp_sum(t1);
-  t2 = warp_sum(t2);
-  if (lane == 0) p.st->counter = 0u;
-  finish_pass(p, t0, t1, t2);
 }
 
 // ---------------------------------------------------------------------------
 // psi <- sum_j C_j q^_j (Eq. 17), q^_1 = psi, q^_j = basis[j-2] for j >= 2.
+// FP64 path: complex128 throughout.  Mixed path: the basis is complex64;
+// C_1 psi is formed in FP64 so that the FP32 rounding of the basis only
+// enters the (small) Krylov corrections.
+// Blocks are dealt to problems in proportion to their size.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) recombine(vec4* psi, const vec4* __restrict__ basis,
-                                                 long long n_sites, DevState* st_) {
+template <bool MIXED>
+__global__ void __launch_bounds__(256) recombine(const __grid_constant__ RecombParams rp) {
   asm volatile("griddepcontrol.wait;" ::: "memory");
   __shared__ double cr[KMAX + 2], ci[KMAX + 2];
+  __shared__ float fr[KMAX + 2], fi[KMAX + 2];
   __shared__ int k_s, err_s;
-  volatile DevState* st = st_;
+  const int b = rp.blk_prob[blockIdx.x];
+  const Problem* pr = rp.probs + b;
+  DevState* st = pr->st;
   if (threadIdx.x == 0) { k_s = st->k_used; err_s = st->error; }
-  if (threadIdx.x <= KMAX) { cr[threadIdx.x] = st->coef_re[threadIdx.x]; ci[threadIdx.x] = st->coef_im[threadIdx.x]; }
+  if (threadIdx.x <= KMAX) {
+    cr[threadIdx.x] = st->coef_re[threadIdx.x];
+    ci[threadIdx.x] = st->coef_im[threadIdx.x];
+    fr[threadIdx.x] = (float)cr[threadIdx.x];
+    fi[threadIdx.x] = (float)ci[threadIdx.x];
+  }
   __syncthreads();
-  if (err_s) return;                                   // leave psi untouched
-  if (blockIdx.x == 0 && threadIdx.x == 0) st->stopped = 0;   // re-arm the next step
+  const int lb = blockIdx.x - pr->rblk_begin;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *rp.step += 1;   // the next step's fields
+  if (err_s) return;                                         // leave psi untouched
+  if (lb == 0 && threadIdx.x == 0) {                         // re-arm the next step
+    st->stopped = 0;
+    st->cur_pass = 1;
+    st->redo_left = rp.redo_budget;
+  }
   const int k = k_s;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n_sites; s += stride) {
-    const vec4 q = psi[s];
-    double ur = cr[1] * q.x - ci[1] * q.y, ui = cr[1] * q.y + ci[1] * q.x;
-    double dr = cr[1] * q.z - ci[1] * q.w, di = cr[1] * q.w + ci[1] * q.z;
-    for (int j = 2; j <= k; ++j) {
-      const vec4 b = basis[(size_t)(j - 2) * n_sites + s];
-      const double a = cr[j], bb = ci[j];
-      ur = fma(a, b.x, fma(-bb, b.y, ur));
-      ui = fma(a, b.y, fma(bb, b.x, ui));
-      dr = fma(a, b.z, fma(-bb, b.w, dr));
-      di = fma(a, b.w, fma(bb, b.z, di));
+  const long long n = (long long)pr->nx * pr->ny;
+  const long long stride = (long long)pr->rblk_count * blockDim.x;
+  vec4* psi = const_cast<vec4*>(pr->psi);
+  if constexpr (!MIXED) {
+    const vec4* basis = static_cast<const vec4*>(pr->basis);
+    for (long long s = (long long)lb * blockDim.x + threadIdx.x; s < n; s += stride) {
+      const vec4 q = psi[s];
+      double ur = cr[1] * q.x - ci[1] * q.y, ui = cr[1] * q.y + ci[1] * q.x;
+      double dr = cr[1] * q.z - ci[1] * q.w, di = cr[1] * q.w + ci[1] * q.z;
+      for (int j = 2; j <= k; ++j) {
+        const vec4 v = basis[(size_t)(j - 2) * n + s];
+        const double a = cr[j], bb = ci[j];
+        ur = fma(a, v.x, fma(-bb, v.y, ur));
+        ui = fma(a, v.y, fma(bb, v.x, ui));
+        dr = fma(a, v.z, fma(-bb, v.w, dr));
+        di = fma(a, v.w, fma(bb, v.z, di));
+      }
+      vec4 o;
+      o.x = ur; o.y = ui; o.z = dr; o.w = di;
+      psi[s] = o;
     }
-    vec4 o;
-    o.x = ur; o.y = ui; o.z = dr; o.w = di;
-    psi[s] = o;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Mixed path: psi <- C_1 psi + sum_{j>=2} C_j q^_j with psi complex128 and the
-// basis complex64.  C_1 psi is formed in FP64 so that the FP32 rounding of the
-// basis only enters the (small) Krylov corrections.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) recombine_mixed(double4_32a* psi, const float4* __restrict__ basis,
-                                                       long long n_sites, DevState* st_) {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  __shared__ double c1r, c1i;
-  __shared__ float cr[KMAX + 2], ci[KMAX + 2];
-  __shared__ int k_s, err_s;
-  volatile DevState* st = st_;
-  if (threadIdx.x == 0) {
-    k_s = st->k_used; err_s = st->error;
-    c1r = st->coef_re[1]; c1i = st->coef_im[1];
-  }
-  if (threadIdx.x <= KMAX) { cr[threadIdx.x] = (float)st->coef_re[threadIdx.x]; ci[threadIdx.x] = (float)st->coef_im[threadIdx.x]; }
-  __syncthreads();
-  if (err_s) return;
-  if (blockIdx.x == 0 && threadIdx.x == 0) st->stopped = 0;
-  const int k = k_s;
-  const double ar = c1r, ai = c1i;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n_sites; s += stride) {
-    float ur = 0.f, ui = 0.f, dr = 0.f, di = 0.f;
-    for (int j = 2; j <= k; ++j) {
-      const float4 b = basis[(size_t)(j - 2) * n_sites + s];
-      const float a = cr[j], bb = ci[j];
-      ur = fmaf(a, b.x, fmaf(-bb, b.y, ur));
-      ui = fmaf(a, b.y, fmaf(bb, b.x, ui));
-      dr = fmaf(a, b.z, fmaf(-bb, b.w, dr));
-      di = fmaf(a, b.w, fmaf(bb, b.z, di));
+  } else {
+    const float4* basis = static_cast<const float4*>(pr->basis);
+    const double ar = cr[1], ai = ci[1];
+    for (long long s = (long long)lb * blockDim.x + threadIdx.x; s < n; s += stride) {
+      float ur = 0.f, ui = 0.f, dr = 0.f, di = 0.f;
+      for (int j = 2; j <= k; ++j) {
+        const float4 v = basis[(size_t)(j - 2) * n + s];
+        const float a = fr[j], bb = fi[j];
+        ur = fmaf(a, v.x, fmaf(-bb, v.y, ur));
+        ui = fmaf(a, v.y, fmaf(bb, v.x, ui));
+        dr = fmaf(a, v.z, fmaf(-bb, v.w, dr));
+        di = fmaf(a, v.w, fmaf(bb, v.z, di));
+      }
+      const vec4 q = psi[s];
+      vec4 o;
+      o.x = fma(ar, q.x, fma(-ai, q.y, (double)ur));
+      o.y = fma(ar, q.y, fma(ai, q.x, (double)ui));
+      o.z = fma(ar, q.z, fma(-ai, q.w, (double)dr));
+      o.w = fma(ar, q.w, fma(ai, q.z, (double)di));
+      psi[s] = o;
     }
-    const double4_32a q = psi[s];
-    double4_32a o;
-    o.x = fma(ar, q.x, fma(-ai, q.y, (double)ur));
-    o.y = fma(ar, q.y, fma(ai, q.x, (double)ui));
-    o.z = fma(ar, q.z, fma(-ai, q.w, (double)dr));
-    o.w = fma(ar, q.w, fma(ai, q.z, (double)di));
-    psi[s] = o;
   }
+  asm volatile("griddepcontrol.launch_dependents;");
 }
 
 // ---------------------------------------------------------------------------

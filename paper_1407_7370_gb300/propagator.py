@@ -19,12 +19,13 @@ class StepInfo:
     energy: float
     alpha: np.ndarray
     beta: np.ndarray
+    kappa_max: float = 0.0
 
 
 def _info(c: nat.StepInfoC) -> StepInfo:
     k = c.k_used
     return StepInfo(k, bool(c.breakdown), c.err_est, c.cum_err, c.norm, c.energy,
-                    np.array(c.alpha[:k]), np.array(c.beta[:k]))
+                    np.array(c.alpha[:k]), np.array(c.beta[:k]), c.kappa_max)
 
 
 def _torch():
@@ -175,3 +176,93 @@ def tridiag_expm_device(alpha, beta, dt: float, lo: float, hi: float) -> np.ndar
     nat.check(nat.lib().dirac_debug_tridiag_expm(a.ctypes.data_as(P), b.ctypes.data_as(P), k, dt,
                                                  lo, hi, vr.ctypes.data_as(P), vi.ctypes.data_as(P)))
     return vr + 1j * vi
+
+
+class BatchPropagator:
+    """Many independent problems advanced together (dirac_batch_* of include/dirac.h).
+
+    grids: list of (nx, ny, dx, dy).  All problems share mass, c, stencil
+    order, boundary, precision, m_max; each has its own state, potential,
+    shift and vector potential.
+    """
+
+    def __init__(self, grids, mass: float = 1.0, c: float = 137.036, order: int = 2,
+                 boundary: str = "periodic", m_max: int = 20, precision: str = "fp64"):
+        L = nat.lib()
+        self.grids = [tuple(g) for g in grids]
+        n = len(self.grids)
+        nx = (ctypes.c_int * n)(*[g[0] for g in self.grids])
+        ny = (ctypes.c_int * n)(*[g[1] for g in self.grids])
+        dx = (ctypes.c_double * n)(*[g[2] for g in self.grids])
+        dy = (ctypes.c_double * n)(*[g[3] for g in self.grids])
+        b = {"periodic": nat.PERIODIC, "dirichlet": nat.DIRICHLET}[boundary]
+        prec = {"fp64": nat.FP64, "mixed": nat.MIXED}[precision]
+        self._b = ctypes.c_void_p()
+        self._stream = _stream_ptr()
+        nat.check(L.dirac_batch_create(ctypes.byref(self._b), n, nx, ny, dx, dy, mass, c, order, b,
+                                       prec, m_max, self._stream))
+
+    @property
+    def n(self) -> int:
+        return len(self.grids)
+
+    def set_fields(self, problem: int, V=None, A=(0.0, 0.0), shift: float = 0.0):
+        ptr = None
+        if V is not None:
+            torch = _torch()
+            nx, ny = self.grids[problem][:2]
+            if V.dtype != torch.float64 or not V.is_cuda or tuple(V.shape) != (ny, nx) \
+                    or not V.is_contiguous():
+                raise ValueError("V must be a contiguous CUDA float64 tensor (ny, nx)")
+            ptr = ctypes.c_void_p(V.data_ptr())
+        nat.check(nat.lib().dirac_batch_set_fields(self._b, problem, ptr, float(A[0]), float(A[1]),
+                                                   float(shift)))
+
+    def set_launch_shape(self, tile_height: int, ctas_per_sm: int = 0):
+        nat.check(nat.lib().dirac_batch_set_launch_shape(self._b, tile_height, ctas_per_sm))
+
+    def steps(self, psis, nsteps: int, dt: float, m: int, tol: float = 0.0, A=None,
+              info: bool = False):
+        """psis: list of CUDA complex128 tensors (ny, nx, 2); A: optional array
+        (nsteps, n_problems, 2) of per-step vector potentials."""
+        if len(psis) != self.n:
+            raise ValueError("need one state per problem")
+        for p, g in zip(psis, self.grids):
+            _check_psi(p, g[1], g[0])
+        ptrs = (ctypes.c_void_p * self.n)(*[p.data_ptr() for p in psis])
+        a_ptr, a_arr = None, None
+        if A is not None:
+            a_arr = np.ascontiguousarray(A, dtype=np.float64).reshape(nsteps, self.n, 2)
+            a_ptr = a_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        out = (nat.StepInfoC * self.n)() if info else None
+        nat.check(nat.lib().dirac_batch_steps(self._b, ptrs, nsteps, dt, m, tol, a_ptr, out))
+        return [_info(o) for o in out] if info else None
+
+    def sync(self):
+        out = (nat.StepInfoC * self.n)()
+        nat.check(nat.lib().dirac_batch_sync(self._b, out))
+        return [_info(o) for o in out]
+
+    def profile(self, enable: bool = True):
+        nat.check(nat.lib().dirac_batch_profile_enable(self._b, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        ms = (ctypes.c_double * nat.KERNEL_KINDS)()
+        n = (ctypes.c_longlong * nat.KERNEL_KINDS)()
+        nat.check(nat.lib().dirac_batch_profile_read(self._b, ms, n))
+        return {"pass": (ms[0], n[0]), "recombine": (ms[1], n[1])}
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(nat.lib().dirac_batch_kernel_launches(self._b))
+
+    def close(self):
+        if getattr(self, "_b", None) is not None and self._b.value:
+            nat.lib().dirac_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,115 @@
+"""Batched propagation: every problem of a batch against the CPU oracle.
+
+The batch advances problems of different sizes together (one launch per
+Lanczos iteration for all of them); each problem must match the oracle run
+alone, within the same tolerances as the single-problem tests.
+"""
+import numpy as np
+import pytest
+
+from oracle import hamiltonian as ham
+from oracle import lanczos as lz
+from paper_1407_7370_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def fp64_tol(steps, dt):
+    return max(1e-10 * steps * dt, 1e-14 * steps)
+
+
+def mixed_tol(steps, dt, hnorm):
+    """1e-5 per unit time, or FP32 rounding (storage and arithmetic) of one
+    application of exp(-iH dt) per step, 2 u32 ||H|| dt, whichever is larger."""
+    return max(1e-5 * steps * dt, 2 * 6e-8 * hnorm * dt * steps)
+
+
+def hnorm(grid, A, V=None, order=2, c=137.036):
+    """Spectral radius bound of the discrete H (free part plus |V|)."""
+    pf = 1.0 if order == 2 else 1.3723
+    px, py = pf / grid.dx + np.max(np.abs(A[..., 0])), pf / grid.dy + np.max(np.abs(A[..., 1]))
+    e = np.sqrt((c * c) ** 2 + c * c * (px * px + py * py))
+    return e + (0.0 if V is None else np.max(np.abs(V)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1407_7370_gb300 import build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+
+
+GRIDS = [(64, 64, 0.1, 0.1), (37, 23, 0.1, 0.13), (16, 48, 0.12, 0.1), (96, 32, 0.1, 0.1),
+         (7, 5, 0.2, 0.2), (128, 96, 0.08, 0.08)]
+
+
+def _problem(k, g):
+    grid = wl.Grid(*g)
+    if k % 2 == 0:
+        psi0 = wl.positive_energy_packet(grid, p0=(5.0 + 2 * k, 1.0))
+    else:
+        psi0 = 0.1 * wl.random_spinor(grid, 50 + k)
+    V = wl.smoothed_coulomb(grid, 1.0 + k, 0.5) if k % 3 == 1 else None
+    return grid, psi0, V
+
+
+@pytest.mark.parametrize("precision,order,boundary,th", [("fp64", 2, "periodic", 32),
+                                                          ("fp64", 4, "dirichlet", 32),
+                                                          ("mixed", 2, "periodic", 32),
+                                                          ("mixed", 2, "periodic", 16),
+                                                          ("mixed", 4, "dirichlet", 16)])
+def test_batch_matches_oracle_per_problem(precision, order, boundary, th):
+    from paper_1407_7370_gb300 import BatchPropagator
+    dt, m, steps = 1e-4, 8, 4
+    bp = BatchPropagator(GRIDS, order=order, boundary=boundary, m_max=m, precision=precision)
+    if precision == "mixed":
+        bp.set_launch_shape(th)
+    probs = [_problem(k, g) for k, g in enumerate(GRIDS)]
+    rng = np.random.default_rng(7)
+    A = rng.uniform(-20, 20, size=(steps, len(GRIDS), 2))
+    for k, (grid, psi0, V) in enumerate(probs):
+        bp.set_fields(k, None if V is None else torch.from_numpy(V).cuda())
+    psis = [torch.from_numpy(p[1].copy()).cuda() for p in probs]
+    infos = bp.steps(psis, steps, dt, m, A=A, info=True)
+    b = ham.DIRICHLET if boundary == "dirichlet" else ham.PERIODIC
+    for k, (grid, psi0, V) in enumerate(probs):
+        op = ham.Operator(grid.nx, grid.ny, grid.dx, grid.dy, order=order, boundary=b, V=V)
+        ref = psi0.copy()
+        for s in range(steps):
+            op.A = tuple(A[s, k])
+            ref, oi = lz.krylov_step(op, ref, dt, m)
+        err = lz.rel_l2(psis[k].cpu().numpy(), ref)
+        tol = fp64_tol(steps, dt) if precision == "fp64" else \
+            mixed_tol(steps, dt, hnorm(grid, A[:, k], V, order))
+        assert err <= tol, (k, err)
+        assert infos[k].k_used == oi.k_used
+
+
+def test_batch_equals_single_problem_runs():
+    from paper_1407_7370_gb300 import BatchPropagator, Propagator
+    dt, m, steps = 1e-4, 10, 3
+    bp = BatchPropagator(GRIDS, m_max=m)
+    probs = [_problem(k, g) for k, g in enumerate(GRIDS)]
+    for k, (grid, psi0, V) in enumerate(probs):
+        bp.set_fields(k, None if V is None else torch.from_numpy(V).cuda(), A=(3.0, -1.0))
+    psis = [torch.from_numpy(p[1].copy()).cuda() for p in probs]
+    bp.steps(psis, steps, dt, m)
+    for k, (grid, psi0, V) in enumerate(probs):
+        single = Propagator(grid.nx, grid.ny, grid.dx, grid.dy, m_max=m)
+        single.set_fields(None if V is None else torch.from_numpy(V).cuda(), A=(3.0, -1.0))
+        p = torch.from_numpy(psi0.copy()).cuda()
+        single.steps(p, steps, dt, m)
+        assert lz.rel_l2(psis[k].cpu().numpy(), p.cpu().numpy()) <= fp64_tol(steps, dt)
+
+
+def test_batch_kernel_launches_do_not_grow_with_problem_count():
+    from paper_1407_7370_gb300 import BatchPropagator
+    bp = BatchPropagator(GRIDS, m_max=6)
+    probs = [_problem(k, g) for k, g in enumerate(GRIDS)]
+    for k in range(len(GRIDS)):
+        bp.set_fields(k)
+    psis = [torch.from_numpy(p[1].copy()).cuda() for p in probs]
+    bp.steps(psis, 2, 1e-4, 6, info=True)
+    assert bp.kernel_launches == 1 + 2 * (6 + 2 + 1)

@@ -233,7 +233,8 @@ def test_host_buffer_call_equals_device_call():
 def test_kernel_launch_count():
     g = wl.Grid(32, 32, 0.1, 0.1)
     _, _, prop = gpu_run(g, wl.positive_energy_packet(g), 1e-4, 7, 3)
-    assert prop.kernel_launches == 1 + 3 * (7 + 1)   # probe + (m passes + recombine) per step
+    # probe + (m passes + 2 spare launches for re-runs + recombine) per step
+    assert prop.kernel_launches == 1 + 3 * (7 + 2 + 1)
 
 
 @pytest.mark.slow
@@ -260,12 +261,20 @@ def test_laser_packet_1024_full_size():
 # ---------------------------------------------------------------------------
 # Mixed path: complex64 basis and FP32 stencil, FP64 scalars and state.
 # Tolerance: relative L2 of psi at most 1e-5 per unit of simulated time
-# against the FP64 oracle, with a floor of 1e-8 per step for short runs (the
-# complex64 rounding of the basis, 6e-8, times the Krylov coefficients beyond
-# the first, at most ~0.1 here).
+# against the FP64 oracle; for runs too short for that to exceed rounding,
+# FP32 rounding of one application of exp(-iH dt) per step, 2 u32 ||H|| dt
+# (u32 = 6e-8, ||H|| from the spectral bound of the discrete operator).
 # ---------------------------------------------------------------------------
-def mixed_tol(steps, dt):
-    return max(1e-5 * steps * dt, 1e-8 * steps)
+def hnorm(grid, A=(0.0, 0.0), V=None, order=2, c=137.036):
+    pf = 1.0 if order == 2 else 1.3723
+    px, py = pf / grid.dx + abs(A[0]), pf / grid.dy + abs(A[1])
+    e = np.sqrt((c * c) ** 2 + c * c * (px * px + py * py))
+    return e + (0.0 if V is None else float(np.max(np.abs(V))))
+
+
+def mixed_tol(steps, dt, hn=None):
+    floor = 0.0 if hn is None else 2 * 6e-8 * hn * dt * steps
+    return max(1e-5 * steps * dt, floor)
 
 
 def test_mixed_free_packet_64_full_run():
@@ -288,9 +297,7 @@ def test_mixed_ragged_and_boundary_grids(nx, ny, order, boundary, hasv, A):
     out, info, _ = gpu_run(g, psi0, dt, m, steps, V=V, A=A, order=order, boundary=boundary,
                            precision="mixed")
     ref, _ = lz.propagate(oracle_op(g, V=V, A=A, order=order, boundary=b), psi0.copy(), dt, m, steps)
-    # a random (white-noise) field has the full spectral width, so the FP32
-    # Krylov corrections are O(1) here: hold it to FP32 rounding, not 1e-5 t
-    assert lz.rel_l2(out, ref) <= 1e-6 * steps
+    assert lz.rel_l2(out, ref) <= mixed_tol(steps, dt, hnorm(g, A, V, order))
 
 
 def test_mixed_step_scalars_match_oracle():
@@ -304,7 +311,7 @@ def test_mixed_step_scalars_match_oracle():
     assert abs(info.energy - oi.energy) <= 1e-9 * abs(oi.energy)
     assert abs(info.norm - oi.norm) <= 1e-7 * oi.norm
     assert np.allclose(info.alpha[:4], oi.alpha[:4] / dt, rtol=1e-6)
-    assert lz.rel_l2(out, ref) <= mixed_tol(1, dt)
+    assert lz.rel_l2(out, ref) <= mixed_tol(1, dt, hnorm(g, (4.0, -2.0), V))
 
 
 @pytest.mark.slow
@@ -317,4 +324,4 @@ def test_mixed_laser_packet_1024_against_closed_form():
     An = pulse_schedule(t0, dt, n, p.a0, p.omega, p.duration)
     out, info, _ = gpu_run(g, psi0, dt, m, n, A_steps=An, precision="mixed")
     exact = free.propagate(oracle_op(g), psi0.copy(), dt, n, pulse=p, t0=t0)
-    assert lz.rel_l2(out, exact) <= mixed_tol(n, dt)
+    assert lz.rel_l2(out, exact) <= 1e-5 * n * dt
