@@ -215,6 +215,33 @@ dirac_status dirac_batch_steps(dirac_batch* batch, void* const* psi_dev, int nst
 /* Wait for the batch's stream and fill info (n_problems entries, may be NULL). */
 dirac_status dirac_batch_sync(dirac_batch* batch, dirac_step_info* info);
 
+/*
+ * Autotuner of the launch shape: times every candidate (tile height x
+ * CTAs per SM) over `steps` steps of the batch on scratch copies of the
+ * states psi_dev (the states themselves and the scalar blocks are left
+ * unchanged), keeps the fastest, and, when the environment variable
+ * DIRAC_AUTOTUNE_CACHE names a file, records the choice there by a
+ * signature of the problem set (precision, stencil, boundary, sizes, m,
+ * GPU) and reuses it on later calls.  A_xy_host: as for dirac_batch_steps
+ * (for `steps` steps) or NULL.  Allocates scratch (the states' size).
+ */
+typedef struct {
+    int tile_height, ctas_per_sm;   /* the chosen shape */
+    double ms_per_step;             /* its measured time */
+    int from_cache;                 /* 1: taken from the cache file */
+    int candidates;                 /* shapes timed */
+} dirac_tune_result;
+
+dirac_status dirac_batch_autotune(dirac_batch* batch, void* const* psi_dev, double dt, int m,
+                                  const double* A_xy_host, int steps, dirac_tune_result* out);
+
+/*
+ * Replay of a captured CUDA graph per step (default on; off: direct
+ * launches).  The kernels and their order are the same either way.
+ */
+dirac_status dirac_batch_use_graphs(dirac_batch* batch, int enable);
+dirac_status dirac_use_graphs(dirac_ctx* ctx, int enable);
+
 /* dirac_profile_enable / dirac_profile_read / dirac_kernel_launches for a batch. */
 dirac_status dirac_batch_profile_enable(dirac_batch* batch, int enable);
 dirac_status dirac_batch_profile_read(dirac_batch* batch, double* ms, long long* launches);

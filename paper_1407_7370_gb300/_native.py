@@ -39,6 +39,12 @@ class ProblemC(ctypes.Structure):
                 ("energy_shift", ctypes.c_double)]
 
 
+class TuneResultC(ctypes.Structure):
+    _fields_ = [("tile_height", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
+                ("ms_per_step", ctypes.c_double), ("from_cache", ctypes.c_int),
+                ("candidates", ctypes.c_int)]
+
+
 class DiracError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__("dirac status %d (%s): %s" % (status, status_string(status), message))
@@ -91,6 +97,9 @@ def lib():
         "dirac_batch_profile_enable": (i, [vp, i]),
         "dirac_batch_profile_read": (i, [vp, dp, ctypes.POINTER(ctypes.c_longlong)]),
         "dirac_batch_kernel_launches": (ctypes.c_longlong, [vp]),
+        "dirac_batch_autotune": (i, [vp, ctypes.POINTER(vp), d, i, dp, i, ctypes.POINTER(TuneResultC)]),
+        "dirac_batch_use_graphs": (i, [vp, i]),
+        "dirac_use_graphs": (i, [vp, i]),
         "dirac_profile_read": (i, [vp, dp, ctypes.POINTER(ctypes.c_longlong)]),
     }
     for name, (res, args) in sig.items():

@@ -271,6 +271,12 @@ struct Engine {
   bool need_probe = true;
   long long launches = 0;
   vec4* psi_own = nullptr;         // staging for the host-buffer call
+  // CUDA graph of one step (captured on a private stream, replayed on `stream`)
+  bool use_graphs = true;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t step_graph = nullptr;
+  std::vector<unsigned char> graph_key;
+  int graph_kernels = 0;
   // per-kernel CUDA-event timing
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -385,6 +391,8 @@ dirac_status Engine::init(int n, const int* nx, const int* ny, const double* dx,
 
 void Engine::release() {
   cudaStreamSynchronize(stream);
+  if (step_graph) cudaGraphExecDestroy(step_graph);
+  if (cap_stream) cudaStreamDestroy(cap_stream);
   for (cudaEvent_t ev : ev_pool) cudaEventDestroy(ev);
   ev_pool.clear();
   if (tab_ev) cudaEventDestroy(tab_ev);
@@ -572,28 +580,69 @@ dirac_status Engine::run(vec4* const* psi, int nsteps, double dt, int m, double 
   LaunchShape ls = shape;
   ls.th = th;
   const bool diri = boundary == DIRAC_DIRICHLET;
-  for (int s = 0; s < nsteps; ++s) {
-    if (need_probe) {
-      lp.pass = 1;
-      lp.probe = 1;
-      CUDA_TRY(mark(KIND_PASS));
-      CUDA_TRY(launch_pass(precision, order, diri, hasv, lp, ls, stream));
-      ++launches;
-      lp.probe = 0;
-      need_probe = false;
-    }
-    // m passes plus the spare launches for re-runs; every problem runs its
-    // own next pass and launches with nothing left to do exit at once
+  if (need_probe) {
+    lp.pass = 1;
+    lp.probe = 1;
+    CUDA_TRY(mark(KIND_PASS));
+    CUDA_TRY(launch_pass(precision, order, diri, hasv, lp, ls, stream));
+    ++launches;
+    lp.probe = 0;
+    need_probe = false;
+  }
+  // One step: m passes plus the spare launches for re-runs (every problem
+  // runs its own next pass; launches with nothing left to do exit at once),
+  // then the recombination.  The launches are the same at every step (the
+  // fields come from the table through the device step counter).
+  auto enqueue_step = [&](cudaStream_t st, bool count) -> dirac_status {
     for (int i = 1; i <= m + lp.redo_budget; ++i) {
       lp.pass = i;
-      CUDA_TRY(mark(KIND_PASS));
-      CUDA_TRY(launch_pass(precision, order, diri, hasv, lp, ls, stream));
-      ++launches;
+      if (count) CUDA_TRY(mark(KIND_PASS));
+      CUDA_TRY(launch_pass(precision, order, diri, hasv, lp, ls, st));
+      if (count) ++launches;
     }
-    CUDA_TRY(mark(KIND_RECOMBINE));
-    CUDA_TRY(launch_recombine(precision, rp, rgrid, stream));
-    ++launches;
-    CUDA_TRY(mark(KIND_END));
+    if (count) CUDA_TRY(mark(KIND_RECOMBINE));
+    CUDA_TRY(launch_recombine(precision, rp, rgrid, st));
+    if (count) {
+      ++launches;
+      CUDA_TRY(mark(KIND_END));
+    }
+    return DIRAC_OK;
+  };
+  if (use_graphs && !profiling && nsteps >= 2) {
+    // capture once per launch configuration, replay every step
+    std::vector<unsigned char> key(sizeof(LaunchParams) + sizeof(RecombParams) + sizeof(LaunchShape) + 3 * sizeof(int));
+    unsigned char* kp = key.data();
+    LaunchParams lk = lp;
+    lk.pass = 0;
+    std::memcpy(kp, &lk, sizeof(lk)); kp += sizeof(lk);
+    std::memcpy(kp, &rp, sizeof(rp)); kp += sizeof(rp);
+    std::memcpy(kp, &ls, sizeof(ls)); kp += sizeof(ls);
+    const int extra[3] = {precision, (int)hasv, rgrid};
+    std::memcpy(kp, extra, sizeof(extra));
+    if (!step_graph || key != graph_key) {
+      if (!cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+      if (step_graph) { cudaGraphExecDestroy(step_graph); step_graph = nullptr; }
+      cudaGraph_t g = nullptr;
+      CUDA_TRY(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
+      dirac_status st = enqueue_step(cap_stream, false);
+      cudaError_t e = cudaStreamEndCapture(cap_stream, &g);
+      if (st != DIRAC_OK) { if (g) cudaGraphDestroy(g); return st; }
+      if (e != cudaSuccess) return fail(DIRAC_ECUDA, "step capture: %s", cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&step_graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) { step_graph = nullptr; return fail(DIRAC_ECUDA, "graph instantiate: %s", cudaGetErrorString(e)); }
+      graph_key = key;
+      graph_kernels = m + lp.redo_budget + 1;
+    }
+    for (int s = 0; s < nsteps; ++s) {
+      CUDA_TRY(cudaGraphLaunch(step_graph, stream));
+      launches += graph_kernels;
+    }
+  } else {
+    for (int s = 0; s < nsteps; ++s) {
+      dirac_status st = enqueue_step(stream, true);
+      if (st != DIRAC_OK) return st;
+    }
   }
   return DIRAC_OK;
 }
@@ -860,6 +909,129 @@ dirac_status dirac_batch_profile_read(dirac_batch* bt, double* ms, long long* la
 }
 
 long long dirac_batch_kernel_launches(const dirac_batch* bt) { return bt ? bt->e.launches : 0; }
+
+dirac_status dirac_batch_use_graphs(dirac_batch* bt, int enable) {
+  if (!bt) return fail(DIRAC_EINVAL, "null batch");
+  bt->e.use_graphs = enable != 0;
+  return DIRAC_OK;
+}
+
+dirac_status dirac_use_graphs(dirac_ctx* ctx, int enable) {
+  if (!ctx) return fail(DIRAC_EINVAL, "null context");
+  ctx->e.use_graphs = enable != 0;
+  return DIRAC_OK;
+}
+
+// Autotuner: time each candidate launch shape on scratch copies of the
+// states (the caller's states and the scalar blocks are left as they were),
+// keep the fastest, remember it in the cache file named by
+// DIRAC_AUTOTUNE_CACHE (one line per problem signature).
+dirac_status dirac_batch_autotune(dirac_batch* bt, void* const* psi_dev, double dt, int m,
+                                  const double* A_xy_host, int steps, dirac_tune_result* out) {
+  if (!bt || !psi_dev) return fail(DIRAC_EINVAL, "null argument");
+  if (steps < 1) return fail(DIRAC_EINVAL, "steps must be >= 1");
+  Engine& e = bt->e;
+  const int np = e.nprob();
+  long long sites = 0;
+  for (const HostProblem& q : e.P) sites += q.n;
+  char sig[256];
+  {
+    int dev = 0;
+    cudaDeviceProp prop;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaGetDeviceProperties(&prop, dev));
+    for (char* c = prop.name; *c; ++c) if (*c == ' ') *c = '_';
+    snprintf(sig, sizeof(sig), "prec=%d,order=%d,bnd=%d,nprob=%d,sites=%lld,m=%d,sm=%d,gpu=%s", e.precision,
+             e.order, e.boundary, np, sites, m, e.shape.n_sm, prop.name);
+  }
+  const char* cache = std::getenv("DIRAC_AUTOTUNE_CACHE");
+  if (cache && cache[0]) {
+    if (FILE* f = std::fopen(cache, "r")) {
+      char line[512], key[300];
+      int th = 0, cap = 0;
+      double ms = 0;
+      bool found = false;
+      while (std::fgets(line, sizeof(line), f)) {
+        if (std::sscanf(line, "%299s %d %d %lf", key, &th, &cap, &ms) == 4 && std::strcmp(key, sig) == 0) {
+          found = true;
+          break;
+        }
+      }
+      std::fclose(f);
+      if (found && (th == 16 || th == 32) && cap >= 0) {
+        e.shape.th = th;
+        e.shape.cta_cap = cap;
+        if (out) { out->tile_height = th; out->ctas_per_sm = cap; out->ms_per_step = ms; out->from_cache = 1; out->candidates = 0; }
+        return DIRAC_OK;
+      }
+    }
+  }
+  // scratch states and a copy of the scalar blocks
+  std::vector<size_t> off(np + 1, 0);
+  for (int b = 0; b < np; ++b) off[b + 1] = off[b] + align256((size_t)e.P[b].n * sizeof(vec4));
+  char* scratch = nullptr;
+  DevState* st_save = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUDA_TRY(cudaMalloc(&scratch, off[np]));
+  cudaError_t ce = cudaMalloc(&st_save, sizeof(DevState) * np);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(st_save, e.d_st, sizeof(DevState) * np, cudaMemcpyDeviceToDevice, e.stream);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  std::vector<vec4*> sp(np);
+  for (int b = 0; b < np; ++b) sp[b] = reinterpret_cast<vec4*>(scratch + off[b]);
+  struct Cand { int th, cap; };
+  std::vector<Cand> cands;
+  if (e.precision == DIRAC_FP64) cands = {{32, 0}, {32, 1}};
+  else cands = {{16, 0}, {16, 4}, {32, 0}, {32, 2}};
+  const LaunchShape keep = e.shape;
+  const bool probe_keep = e.need_probe;
+  double best = 1e300;
+  Cand pick = cands[0];
+  dirac_status s = DIRAC_OK;
+  for (const Cand& cd : cands) {
+    if (ce != cudaSuccess) break;
+    for (int b = 0; b < np && ce == cudaSuccess; ++b)
+      ce = cudaMemcpyAsync(sp[b], psi_dev[b], (size_t)e.P[b].n * sizeof(vec4), cudaMemcpyDeviceToDevice, e.stream);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(e.d_st, st_save, sizeof(DevState) * np, cudaMemcpyDeviceToDevice, e.stream);
+    if (ce != cudaSuccess) break;
+    e.need_probe = true;
+    e.shape.th = cd.th;
+    e.shape.cta_cap = cd.cap;
+    s = e.run(sp.data(), 1, dt, m, 0.0, A_xy_host);                       // warm-up
+    if (s == DIRAC_OK) ce = cudaEventRecord(e0, e.stream);
+    if (s == DIRAC_OK && ce == cudaSuccess) s = e.run(sp.data(), steps, dt, m, 0.0, A_xy_host);
+    if (s == DIRAC_OK && ce == cudaSuccess) ce = cudaEventRecord(e1, e.stream);
+    if (s == DIRAC_OK && ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+    if (s != DIRAC_OK || ce != cudaSuccess) break;
+    float ms = 0.f;
+    ce = cudaEventElapsedTime(&ms, e0, e1);
+    const double per = ms / steps;
+    if (per < best) { best = per; pick = cd; }
+  }
+  // leave everything as it was, with the chosen shape
+  if (ce == cudaSuccess && st_save) ce = cudaMemcpyAsync(e.d_st, st_save, sizeof(DevState) * np, cudaMemcpyDeviceToDevice, e.stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(e.stream);
+  e.need_probe = probe_keep;
+  cudaFree(scratch);
+  cudaFree(st_save);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (s != DIRAC_OK) { e.shape = keep; return s; }
+  if (ce != cudaSuccess) { e.shape = keep; return fail(DIRAC_ECUDA, "autotune: %s", cudaGetErrorString(ce)); }
+  e.shape.th = pick.th;
+  e.shape.cta_cap = pick.cap;
+  if (cache && cache[0]) {
+    if (FILE* f = std::fopen(cache, "a")) {
+      std::fprintf(f, "%s %d %d %.6f\n", sig, pick.th, pick.cap, best);
+      std::fclose(f);
+    }
+  }
+  if (out) {
+    out->tile_height = pick.th; out->ctas_per_sm = pick.cap; out->ms_per_step = best;
+    out->from_cache = 0; out->candidates = (int)cands.size();
+  }
+  return DIRAC_OK;
+}
 
 // ----------------------------- test hook -----------------------------------
 

@@ -126,6 +126,9 @@ class Propagator:
     def sync(self):
         nat.check(nat.lib().dirac_sync(self._ctx))
 
+    def use_graphs(self, enable: bool = True):
+        nat.check(nat.lib().dirac_use_graphs(self._ctx, 1 if enable else 0))
+
     def profile(self, enable: bool = True):
         """Start/stop per-kernel CUDA-event timing (see dirac_profile_enable)."""
         nat.check(nat.lib().dirac_profile_enable(self._ctx, 1 if enable else 0))
@@ -237,6 +240,22 @@ class BatchPropagator:
         out = (nat.StepInfoC * self.n)() if info else None
         nat.check(nat.lib().dirac_batch_steps(self._b, ptrs, nsteps, dt, m, tol, a_ptr, out))
         return [_info(o) for o in out] if info else None
+
+    def autotune(self, psis, dt: float, m: int, A=None, steps: int = 3) -> dict:
+        """Pick the fastest launch shape (see dirac_batch_autotune); states unchanged."""
+        ptrs = (ctypes.c_void_p * self.n)(*[p.data_ptr() for p in psis])
+        a_ptr, a_arr = None, None
+        if A is not None:
+            a_arr = np.ascontiguousarray(A, dtype=np.float64).reshape(steps, self.n, 2)
+            a_ptr = a_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        r = nat.TuneResultC()
+        nat.check(nat.lib().dirac_batch_autotune(self._b, ptrs, dt, m, a_ptr, steps, ctypes.byref(r)))
+        return {"tile_height": r.tile_height, "ctas_per_sm": r.ctas_per_sm,
+                "ms_per_step": r.ms_per_step, "from_cache": bool(r.from_cache),
+                "candidates": r.candidates}
+
+    def use_graphs(self, enable: bool = True):
+        nat.check(nat.lib().dirac_batch_use_graphs(self._b, 1 if enable else 0))
 
     def sync(self):
         out = (nat.StepInfoC * self.n)()

@@ -113,3 +113,47 @@ def test_batch_kernel_launches_do_not_grow_with_problem_count():
     psis = [torch.from_numpy(p[1].copy()).cuda() for p in probs]
     bp.steps(psis, 2, 1e-4, 6, info=True)
     assert bp.kernel_launches == 1 + 2 * (6 + 2 + 1)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_graph_replay_equals_direct_launches(precision):
+    from paper_1407_7370_gb300 import BatchPropagator
+    probs = [_problem(k, g) for k, g in enumerate(GRIDS)]
+    A = np.random.default_rng(3).uniform(-5, 5, size=(6, len(GRIDS), 2))
+    outs = []
+    for graphs in (True, False):
+        bp = BatchPropagator(GRIDS, m_max=8, precision=precision)
+        bp.use_graphs(graphs)
+        for k, (grid, psi0, V) in enumerate(probs):
+            bp.set_fields(k, None if V is None else torch.from_numpy(V).cuda())
+        psis = [torch.from_numpy(p[1].copy()).cuda() for p in probs]
+        bp.steps(psis, 6, 1e-4, 8, A=A)
+        outs.append([p.cpu().numpy() for p in psis])
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+
+
+def test_autotune_leaves_states_and_picks_a_shape(tmp_path, monkeypatch):
+    from paper_1407_7370_gb300 import BatchPropagator
+    monkeypatch.setenv("DIRAC_AUTOTUNE_CACHE", str(tmp_path / "tune.txt"))
+    probs = [_problem(k, g) for k, g in enumerate(GRIDS)]
+    bp = BatchPropagator(GRIDS, m_max=8, precision="mixed")
+    for k, (grid, psi0, V) in enumerate(probs):
+        bp.set_fields(k, None if V is None else torch.from_numpy(V).cuda())
+    psis = [torch.from_numpy(p[1].copy()).cuda() for p in probs]
+    r = bp.autotune(psis, 1e-4, 8, steps=2)
+    assert r["tile_height"] in (16, 32) and r["candidates"] >= 2 and not r["from_cache"]
+    for p, (grid, psi0, V) in zip(psis, probs):
+        assert np.array_equal(p.cpu().numpy(), psi0)
+    # the choice is reused from the cache file by an identical batch
+    bp2 = BatchPropagator(GRIDS, m_max=8, precision="mixed")
+    r2 = bp2.autotune(psis, 1e-4, 8, steps=2)
+    assert r2["from_cache"] and r2["tile_height"] == r["tile_height"]
+    # and stepping after tuning still matches the oracle
+    for k in range(len(GRIDS)):
+        bp.set_fields(k, None if probs[k][2] is None else torch.from_numpy(probs[k][2]).cuda())
+    bp.steps(psis, 2, 1e-4, 8)
+    grid, psi0, V = probs[0]
+    op = ham.Operator(grid.nx, grid.ny, grid.dx, grid.dy, V=V)
+    ref, _ = lz.propagate(op, psi0.copy(), 1e-4, 8, 2)
+    assert lz.rel_l2(psis[0].cpu().numpy(), ref) <= mixed_tol(2, 1e-4, hnorm(grid, np.zeros((1, 2)), V))
