@@ -43,7 +43,7 @@ PASS_FLOPS_PER_SITE = 80   # FP64 flops of one Lanczos iteration per site (see D
 
 # DRAM traffic per launch from the last ncu capture of the pass kernel, valid
 # only for the kernel source it was taken with (sha1 of dirac_kernels.cuh).
-TRAFFIC = {}
+TRAFFIC = {"fp64": ("a5693c562fe9", 69.62e6 + 20.36e6), "mixed": ("a5693c562fe9", 33.62e6 + 0.62e6)}
 
 
 def kernel_sha() -> str:
@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
     ap.add_argument("--only", choices=["fp64", "mixed"], default=None,
                     help="run one path only (for profiling); prints a partial line")
     return ap.parse_args()
@@ -239,6 +240,88 @@ def measure(prop, psi, A, K, W, world, dist, torch, gi):
                 te=te, Ke=Ke)
 
 
+def measure_batch(args, torch, world, dist, gi, pk):
+    """The batched workload: mixed path (autotuned, graph-replayed) and, for
+    comparison on the same GPU, the plain FP64 path over fewer steps."""
+    from paper_1407_7370_gb300 import BatchPropagator
+    from paper_1407_7370_gb300.propagator import pulse_sin2_mean
+    cfg = wl.BATCH_256
+    grids, p0s, a0s = wl.batch_packets(cfg["n"])
+    m, dt, n = cfg["m"], cfg["dt"], cfg["n"]
+    sites = int(sum(g.n_sites for g in grids))
+    psi0 = [wl.positive_energy_packet(g, p0=(float(p), 0.0)) for g, p in zip(grids, p0s)]
+    W = args.warmup
+    K = max(5, min(args.steps, 60))
+    K64 = max(3, K // 12)
+    KC = 200                      # steps of the mixed-vs-FP64 comparison
+    tot = max(W + 2 * K + 8, KC)
+    base = np.array([pulse_sin2_mean(k * dt, dt, 1.0, cfg["pulse"].omega, cfg["pulse"].duration)
+                     for k in range(tot)])
+    A = np.zeros((tot, n, 2))
+    A[:, :, 0] = base[:, None] * a0s[None, :]
+    out = {}
+    results = {}
+    for prec, steps in (("mixed", K), ("fp64", K64)):
+        bp = BatchPropagator([(g.nx, g.ny, g.dx, g.dy) for g in grids], m_max=m, precision=prec)
+        for k in range(n):
+            bp.set_fields(k)
+        psis = [torch.from_numpy(p).cuda() for p in psi0]
+        tune = bp.autotune(psis, dt, m, A=A[:3], steps=3)
+        bp.steps(psis, W, dt, m, A=A[:W])
+        torch.cuda.synchronize()
+        clocks = ClockSampler(gi)
+        clocks.start()
+        l0 = bp.kernel_launches
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream = torch.cuda.current_stream()
+        e0.record(stream)
+        bp.steps(psis, steps, dt, m, A=A[W:W + steps])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        launches = bp.kernel_launches - l0
+        clk = clocks.stop()
+        t = e0.elapsed_time(e1) / 1e3
+        bp.profile(True)
+        bp.steps(psis, steps, dt, m, A=A[W + steps:W + 2 * steps])
+        prof = bp.profile_read()
+        bp.profile(False)
+        infos = bp.sync()
+        # a shared stretch for the error statement: K64 steps from psi0
+        cmp = [torch.from_numpy(psi0[k]).cuda() for k in range(0, n, 32)]
+        sub = BatchPropagator([(grids[k].nx, grids[k].ny, grids[k].dx, grids[k].dy)
+                               for k in range(0, n, 32)], m_max=m, precision=prec)
+        for j in range(len(cmp)):
+            sub.set_fields(j)
+        sub.steps(cmp, KC, dt, m, A=A[:KC, ::32])
+        results[prec] = [c.cpu().numpy() for c in cmp]
+        sub.close()
+        pass_ms, pass_n = prof["pass"]
+        rec_ms, rec_n = prof["recombine"]
+        sb = 16 if prec == "mixed" else 32
+        # launch-average pass time covers the spare launches too: use the
+        # pass time per step divided by m (the algorithmic passes)
+        per_pass = pass_ms / 1e3 / steps / m
+        gbs = 3 * sb * sites / per_pass / 1e9
+        out[prec] = {"value": world * sites * m * steps / t, "unit": UNIT,
+                     "ms_per_step": 1e3 * t / steps, "steps": steps, "gpu_launches": launches,
+                     "autotune": tune, "clocks": clk,
+                     "pass_time_per_step_ms": pass_ms / steps, "recombine_ms_per_step": rec_ms / steps,
+                     "kappa_max": max(i.kappa_max for i in infos),
+                     "hbm_algorithmic": {"achieved": gbs, "peak": pk.get("hbm_gbs", 6800.0),
+                                         "unit": "GB/s", "frac": gbs / pk.get("hbm_gbs", 6800.0),
+                                         "bytes_per_site_per_pass": 3 * sb}}
+        bp.close()
+        del psis
+        torch.cuda.empty_cache()
+    err = max(float(np.linalg.norm(a - b) / np.linalg.norm(b))
+              for a, b in zip(results["mixed"], results["fp64"]))
+    return {"workload": cfg["name"], "sites": sites, "problems": n, "mixed": out["mixed"],
+            "fp64": out["fp64"],
+            "mixed_vs_fp64": {"max_rel_l2": err, "per_unit_time": err / (KC * dt), "steps": KC,
+                              "problems_compared": len(results["mixed"])},
+            "speedup_mixed_batched_vs_fp64_single": None}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -274,9 +357,11 @@ def run_ours(args):
         return world * g.n_sites * m * steps / t
 
     def kernel_stats(r):
+        # per algorithmic pass: the pass-kernel time of a step over m (the
+        # spare launches kept for re-runs carry no data and are included)
         pass_ms, pass_n = r["prof"]["pass"]
         rec_ms, rec_n = r["prof"]["recombine"]
-        return pass_ms / pass_n / 1e3, pass_ms / (pass_ms + rec_ms), rec_ms / max(1, rec_n) / 1e3
+        return (pass_ms / K / m / 1e3, pass_ms / (pass_ms + rec_ms), rec_ms / max(1, rec_n) / 1e3)
 
     if args.only:
         r = runs[args.only]
@@ -343,6 +428,10 @@ def run_ours(args):
                 "diagnostics": {"k_used": f["info"].k_used, "err_est_last": f["info"].err_est,
                                 "cum_err_est": f["info"].cum_err, "energy": f["info"].energy,
                                 "recombine_avg_us": f_rec * 1e6}}
+        if not args.no_batch:
+            line["batched"] = measure_batch(args, torch, world, dist, local, pk)
+            line["batched"]["speedup_mixed_batched_vs_fp64_single"] = \
+                line["batched"]["mixed"]["value"] / line["value"]
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline()
         elif not args.no_cpu_baseline:
