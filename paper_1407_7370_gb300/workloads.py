@@ -134,3 +134,21 @@ LASER_PACKET_1024 = dict(
     name="laser packet 1024x1024, dx=0.05, m=20, dt=2e-4, 5000 steps",
     grid=Grid(1024, 1024, 0.05, 0.05), p0=(10.0, 0.0), sigma_x=1.0, m=20,
     dt=2e-4, steps=5000, pulse=SinSquaredPulse(50.0, 0.05, 1.0), order=2)
+
+
+def batch_packets(n: int = 256, seed: int = 0, sides=(128, 256, 384, 512), dx: float = 0.05):
+    """The batched workload: n packets on square grids drawn uniformly from
+    `sides`, mean momenta p0 = (U[0, 50], 0) au and laser amplitudes
+    A0 = U[0, 100] au (each packet in A0 sin^2(pi t) sin(0.05 t)), seeded.
+    Returns (grids, p0s, a0s)."""
+    rng = np.random.default_rng(seed)
+    s = rng.choice(np.asarray(sides), size=n)
+    p0s = rng.uniform(0.0, 50.0, size=n)
+    a0s = rng.uniform(0.0, 100.0, size=n)
+    grids = [Grid(int(k), int(k), dx, dx) for k in s]
+    return grids, p0s, a0s
+
+
+BATCH_256 = dict(
+    name="256 packets on 128^2..512^2 grids, dx=0.05, m=16, dt=2e-4, 2000 steps",
+    n=256, m=16, dt=2e-4, steps=2000, pulse=SinSquaredPulse(1.0, 0.05, 1.0))
