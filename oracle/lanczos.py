@@ -147,30 +147,55 @@ def propagate(op: ham.Operator, psi: np.ndarray, dt: float, m: int, steps: int,
 
 @dataclasses.dataclass
 class EigResult:
-    values: np.ndarray      # converged Ritz values in the window, ascending
-    bounds: np.ndarray      # their Eq. 9 bounds |beta_k t_i^k|
+    values: np.ndarray      # selected Ritz values (energies of H - shift), ascending
+    bounds: np.ndarray      # their error bounds (Eq. 9; folded mode: see lanczos_eigs)
     iterations: int
-    all_ritz: np.ndarray    # every Ritz value at the last iteration
+    all_ritz: np.ndarray    # every Ritz value of the recurrence's operator at the end
     all_bounds: np.ndarray
+    breakdown: bool = False
+    vectors: list = None    # Ritz vectors Q t_i (Eq. 8) of the selected values, if asked
 
 
 def lanczos_eigs(op: ham.Operator, start: np.ndarray, n_want: int, max_iter: int,
-                 tol: float, window: tuple, reorth: bool = True, check_every: int = 10):
-    """Eigenvalue mode (Sec. 2, Sec. 5): Ritz values of (H - shift) with Eq. 9 bounds.
+                 tol: float, window: tuple, reorth: bool = True, check_every: int = 10,
+                 fold=None, vectors: bool = False):
+    """Eigenvalue mode (Sec. 2, Sec. 5): Ritz values with Eq. 9 bounds.
 
-    Each iteration: z = A q_i - beta_{i-1} q_{i-1}; alpha_i = q_i . z; then,
-    with ``reorth``, z is orthogonalised against all previous Lanczos vectors
-    by classical Gram-Schmidt, twice, and the coefficients along q_i are added
-    to alpha_i.  Every ``check_every`` iterations (and at the end) T is
-    diagonalised; a Ritz value counts as converged when its bound is
-    <= tol * max(1, |theta|).  Stops when ``n_want`` converged Ritz values lie
-    inside ``window`` (open interval, energies of H - shift).
+    The recurrence runs on A = H - shift (``fold`` None) or, shift-folded, on
+    A = (H - shift - fold)^2, whose smallest eigenvalues belong to the
+    eigenvalues of H - shift nearest ``fold``.  Each iteration:
+    z = A q_i - beta_{i-1} q_{i-1}; alpha_i = q_i . z; z -= alpha_i q_i; with
+    ``reorth``, z is orthogonalised against all previous Lanczos vectors by
+    classical Gram-Schmidt, twice, and the coefficients along q_i are added to
+    alpha_i; beta_i = ||z||.  The recurrence ends at the breakdown test of the
+    propagator (beta_i <= 1e-12 * scale, T's spectrum is then exact).
+
+    Every ``check_every`` iterations (and at the end) T is diagonalised.  A Ritz
+    value theta counts as converged when its bound |beta_k t_i^k| (Eq. 9) is
+    <= tol * max(1, |theta|).
+      direct: stop when ``n_want`` converged Ritz values lie in ``window`` (open
+        interval, energies of H - shift); all of them are returned.
+      folded: stop when the ``n_want`` smallest Ritz values of A are converged;
+        each gives lambda = fold + sign sqrt(theta), the sign being that of the
+        Rayleigh quotient of its Ritz vector with H - shift - fold, and the
+        bound min(sqrt(r), r / sqrt(theta)) on |lambda - lambda_exact| from the
+        Eq. 9 bound r on theta.  ``window`` is not used.
+    With ``vectors`` the Ritz vectors Q t_i (Eq. 8, unit norm) of the returned
+    values are returned too.
     """
+    if fold is None:
+        def apply_a(v):
+            return ham.apply(op, v)
+        ashift = op.shift             # scale of the breakdown test as in the propagator
+    else:
+        def apply_f(v):
+            return ham.apply(op, v) - fold * v
+        def apply_a(v):
+            return apply_f(apply_f(v))
+        ashift = 0.0
     q = [start / ham.norm(start)]
     alpha, beta = [], []
-    z = ham.apply(op, q[0])
-    it = 0
-    theta = bnd = np.zeros(0)
+    z = apply_a(q[0])
     while True:
         i = len(alpha)
         a = ham.inner(q[i], z).real
@@ -185,18 +210,42 @@ def lanczos_eigs(op: ham.Operator, start: np.ndarray, n_want: int, max_iter: int
         alpha.append(a)
         beta.append(bt)
         it = i + 1
-        done = it >= max_iter
+        scale = max(max(abs(x + ashift) for x in alpha), max(beta[:-1]) if it > 1 else 0.0)
+        broke = bt <= BREAKDOWN_REL * scale
+        done = it >= max_iter or broke
         if it % check_every == 0 or done:
             theta, S = scipy.linalg.eigh_tridiagonal(np.array(alpha), np.array(beta[:-1])) \
                 if it > 1 else (np.array(alpha), np.ones((1, 1)))
             bnd = np.abs(bt * S[-1, :])
-            conv = (bnd <= tol * np.maximum(1.0, np.abs(theta))) & \
-                   (theta > window[0]) & (theta < window[1])
-            if conv.sum() >= n_want or done:
-                sel = np.nonzero(conv)[0]
-                return EigResult(theta[sel], bnd[sel], it, theta, bnd)
+            conv = bnd <= tol * np.maximum(1.0, np.abs(theta))
+            if fold is None:
+                conv &= (theta > window[0]) & (theta < window[1])
+                finished = conv.sum() >= n_want
+            else:
+                finished = theta.size >= n_want and bool(conv[:n_want].all())
+            if finished or done:
+                sel = np.nonzero(conv)[0] if fold is None else \
+                    np.nonzero(conv[:n_want])[0]
+                vecs = None
+                if vectors or fold is not None:
+                    Q = np.stack([v.reshape(-1) for v in q], axis=1)
+                    vecs = [(Q @ S[:, j]).reshape(start.shape) for j in sel]
+                vals, bnds = theta[sel], bnd[sel]
+                if fold is not None:
+                    lam, lb = [], []
+                    for j, y in zip(sel, vecs):
+                        rq = ham.inner(y, apply_f(y)).real
+                        th = max(theta[j], 0.0)
+                        lam.append(fold + np.copysign(np.sqrt(th), rq))
+                        lb.append(min(np.sqrt(bnd[j]), bnd[j] / np.sqrt(th)) if th > 0
+                                  else np.sqrt(bnd[j]))
+                    order = np.argsort(lam, kind="stable")
+                    vals, bnds = np.asarray(lam)[order], np.asarray(lb)[order]
+                    vecs = [vecs[o] for o in order]
+                return EigResult(vals, bnds, it, theta, bnd, bool(broke),
+                                 vecs if vectors else None)
         q.append(z / bt)
-        z = ham.apply(op, q[i + 1]) - bt * q[i]
+        z = apply_a(q[i + 1]) - bt * q[i]
 
 
 def energy(op: ham.Operator, psi: np.ndarray) -> float:
