@@ -290,6 +290,77 @@ dirac_status dirac_lanczos_step_noalloc(const dirac_problem* problem, void* psi_
 /* Size in bytes of the static scratch array used by dirac_lanczos_step_noalloc. */
 size_t dirac_noalloc_scratch_bytes(void);
 
+/* ------------------------------------------------------------------------
+ * Hamiltonian product and eigenvalue mode (Sec. 2, Sec. 5)
+ * ------------------------------------------------------------------------ */
+
+/*
+ * out = (H - s) in for the context's operator and fields (Eq. 12 with the
+ * V, A and energy shift s of dirac_set_fields), in FP64 whatever the
+ * context's precision.  in, out: complex128 [ny][nx][2] device fields,
+ * 32-byte aligned, not aliased.  Asynchronous on the context stream.
+ * Errors: DIRAC_EINVAL (null, unaligned or aliased pointers), DIRAC_ESTATE
+ * (fields not set), DIRAC_ECUDA.
+ */
+dirac_status dirac_apply_hamiltonian(dirac_ctx* ctx, const void* in_dev, void* out_dev);
+
+/* Most Ritz values examined per convergence check (and so largest n_want). */
+#define DIRAC_EIG_RITZ_MAX 256
+/* Largest Lanczos iteration count of the eigenvalue mode. */
+#define DIRAC_EIG_ITER_MAX 8192
+
+typedef struct {
+    int iterations;    /* Lanczos iterations k run (size of T_k at the end) */
+    int n_found;       /* values written to eigs_out */
+    int n_in_window;   /* Ritz values of T_k in the window (folded: k) */
+    int n_converged;   /* of those examined, with bound <= tol * max(1, |theta|) */
+    int breakdown;     /* 1: beta_k fell below 1e-12 * scale, T_k's spectrum is exact */
+} dirac_eig_info;
+
+/*
+ * Eigenvalues of H - s near the bottom of the band gap, by the Lanczos
+ * algorithm with full reorthogonalisation (classical Gram-Schmidt applied
+ * twice, Sec. 2; reorth = 0: the plain three-term recurrence of Fig. 1).
+ *
+ * The recurrence runs on A = H - s (fold = 0) or on A = (H - s - sigma)^2
+ * (fold = 1), starting from start_dev (complex128 [ny][nx][2], any nonzero
+ * norm; not modified).  Every check_every iterations and at max_iter the Ritz
+ * values theta of T_k and their Eq. 9 bounds |beta_k t_i^k| are computed on
+ * the device; theta counts as converged when its bound is
+ * <= tol * max(1, |theta|).
+ *   fold = 0: stops when n_want converged Ritz values lie in the open window
+ *     (e_lo, e_hi) (energies of H - s; the bound states of a potential that
+ *     vanishes at infinity lie in (-s, mc^2 - s), Sec. 5).  Returns the lowest
+ *     n_want converged ones, ascending, with their bounds.
+ *   fold = 1: stops when the n_want smallest Ritz values of A are converged;
+ *     each gives lambda = sigma + sign(rho) sqrt(theta), rho the Rayleigh
+ *     quotient of its Ritz vector with H - s - sigma, bound
+ *     min(sqrt(r), r / sqrt(theta)) from the Eq. 9 bound r; returned
+ *     ascending in lambda.  e_lo, e_hi are not used.
+ * At a breakdown (invariant subspace) the recurrence stops and T_k's spectrum
+ * is exact.  At most DIRAC_EIG_RITZ_MAX Ritz values (the lowest in the window)
+ * are examined per check.
+ *
+ * eigs_out, bounds_out: host arrays of n_want doubles; the first
+ * info->n_found entries are written.  vecs_dev: NULL, or room for n_want
+ * device fields (complex128 [ny][nx][2] each, consecutive, 32-byte aligned)
+ * that receive the unit-norm Ritz vectors Q t_i (Eq. 8) of the returned
+ * values.  info may be NULL.
+ *
+ * Device memory: (max_iter + 1) fields for the basis (plus 1 + n_want with
+ * fold = 1), allocated for the call and freed before it returns; the call
+ * synchronises the context stream at every check.
+ * Errors: DIRAC_EINVAL (n_want outside 1..DIRAC_EIG_RITZ_MAX, max_iter
+ * outside 1..DIRAC_EIG_ITER_MAX, check_every < 1, tol < 0, e_lo >= e_hi,
+ * null outputs, unaligned pointers), DIRAC_ESTATE (fields not set),
+ * DIRAC_ENOMEM (the basis does not fit), DIRAC_ENONFINITE (NaN/Inf met, or a
+ * zero start vector), DIRAC_ECUDA.
+ */
+dirac_status dirac_lanczos_eigs(dirac_ctx* ctx, const void* start_dev, int n_want, int max_iter,
+                                int check_every, double tol, double e_lo, double e_hi, int reorth,
+                                int fold, double sigma, double* eigs_out, double* bounds_out,
+                                void* vecs_dev, dirac_eig_info* info);
+
 /*
  * Test hook for the device small-matrix exponential: v = exp(-i T dt) e_1 for
  * the k-by-k tridiagonal T (alpha[0..k-1] diagonal, beta[0..k-2] off

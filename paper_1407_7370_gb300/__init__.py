@@ -6,6 +6,6 @@ Dirac Hamiltonian (Sec. 3-4 and 7 of the paper).  All work runs in the CUDA
 library behind ``include/dirac.h``; PyTorch tensors only provide device memory
 and the stream.
 """
-from .propagator import (BatchPropagator, Propagator, StepInfo, pulse_sin2_mean,  # noqa: F401
+from .propagator import (BatchPropagator, EigResult, Propagator, StepInfo, pulse_sin2_mean,  # noqa: F401
                          tridiag_expm_device)
 from . import workloads  # noqa: F401

@@ -16,6 +16,8 @@ _lib = None
 HEADER = os.path.join(_build.ROOT, "include", "dirac.h")
 KRYLOV_MAX = 32
 KERNEL_KINDS = 2
+EIG_RITZ_MAX = 256
+EIG_ITER_MAX = 8192
 
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ESTATE = range(6)
 PERIODIC, DIRICHLET = 0, 1
@@ -43,6 +45,12 @@ class TuneResultC(ctypes.Structure):
     _fields_ = [("tile_height", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
                 ("ms_per_step", ctypes.c_double), ("from_cache", ctypes.c_int),
                 ("candidates", ctypes.c_int)]
+
+
+class EigInfoC(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("n_found", ctypes.c_int),
+                ("n_in_window", ctypes.c_int), ("n_converged", ctypes.c_int),
+                ("breakdown", ctypes.c_int)]
 
 
 class DiracError(RuntimeError):
@@ -101,6 +109,9 @@ def lib():
         "dirac_batch_use_graphs": (i, [vp, i]),
         "dirac_use_graphs": (i, [vp, i]),
         "dirac_profile_read": (i, [vp, dp, ctypes.POINTER(ctypes.c_longlong)]),
+        "dirac_apply_hamiltonian": (i, [vp, vp, vp]),
+        "dirac_lanczos_eigs": (i, [vp, vp, i, i, i, d, d, d, i, i, d, dp, dp, vp,
+                                   ctypes.POINTER(EigInfoC)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -7,8 +7,9 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SOURCES = [os.path.join(HERE, "csrc", "dirac_capi.cu")]
+SOURCES = [os.path.join(HERE, "csrc", "dirac_capi.cu"), os.path.join(HERE, "csrc", "dirac_eigs.cu")]
 DEPS = SOURCES + [os.path.join(HERE, "csrc", "dirac_kernels.cuh"),
+                  os.path.join(HERE, "csrc", "dirac_internal.h"),
                   os.path.join(ROOT, "include", "dirac.h")]
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libdirac_gb300.so")
@@ -37,15 +38,38 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc_path(), "-std=c++17", "-O3", "-lineinfo", "-gencode", ARCH,
-           "-Xcompiler", "-fPIC", "-shared", "-I", os.path.join(ROOT, "include"),
-           "-o", tmp] + SOURCES
+    tag = ".tmp%d" % os.getpid()
+    nvcc = nvcc_path()
+    flags = ["-std=c++17", "-O3", "-lineinfo", "-gencode", ARCH, "-Xcompiler", "-fPIC",
+             "-I", os.path.join(ROOT, "include")]
+    # one object per translation unit, compiled in parallel, then one link
+    objs, procs = [], []
+    for src in SOURCES:
+        obj = os.path.join(OUT_DIR, os.path.basename(src) + tag + ".o")
+        cmd = [nvcc] + flags + ["-c", src, "-o", obj]
+        objs.append(obj)
+        procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT,
+                                            text=True)))
+    out, bad = [], None
+    for cmd, p in procs:
+        text, _ = p.communicate()
+        out.append(text)
+        if p.returncode != 0 and bad is None:
+            bad = "nvcc failed:\n" + " ".join(cmd) + "\n" + text
+    if bad is not None:
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
+        raise RuntimeError(bad)
+    tmp = LIB + tag
+    cmd = [nvcc, "-shared", "-gencode", ARCH, "-o", tmp] + objs
     res = subprocess.run(cmd, capture_output=True, text=True)
+    for o in objs:
+        os.remove(o)
     if res.returncode != 0:
-        raise RuntimeError("nvcc failed:\n" + " ".join(cmd) + "\n" + res.stdout + res.stderr)
+        raise RuntimeError("nvcc link failed:\n" + " ".join(cmd) + "\n" + res.stdout + res.stderr)
     if verbose:
-        print(res.stdout + res.stderr)
+        print("".join(out) + res.stdout + res.stderr)
     os.replace(tmp, LIB)
     return LIB
 

@@ -1,6 +1,7 @@
 // dirac_capi.cu -- host side of the GB300 Dirac Lanczos propagator: problem
 // tables, workspace, launch sequencing and the C ABI of include/dirac.h.
 #include "dirac.h"
+#include "dirac_internal.h"
 #include "dirac_kernels.cuh"
 
 #include <cuda_runtime.h>
@@ -18,7 +19,7 @@
 
 using namespace dirac;
 
-namespace {
+namespace dirac {
 
 thread_local char g_err[512] = "";
 
@@ -29,6 +30,10 @@ dirac_status fail(dirac_status s, const char* fmt, ...) {
   va_end(ap);
   return s;
 }
+
+}  // namespace dirac
+
+namespace {
 
 #define CUDA_TRY(call)                                                                  \
   do {                                                                                  \
@@ -243,6 +248,7 @@ struct HostProblem {
   void* basis = nullptr;
   void* ybuf[2] = {nullptr, nullptr};
   void* V = nullptr;               // double (FP64) or float (mixed) copy
+  double* V64 = nullptr;           // double copy (== V on the FP64 path)
   bool has_v = false;
   double vmin = 0, vmax = 0;
   double ax = 0, ay = 0, shift = 0;
@@ -397,7 +403,10 @@ void Engine::release() {
   ev_pool.clear();
   if (tab_ev) cudaEventDestroy(tab_ev);
   cudaFree(vec_mem);
-  for (HostProblem& q : P) cudaFree(q.V);
+  for (HostProblem& q : P) {
+    if (q.V64 != q.V) cudaFree(q.V64);
+    cudaFree(q.V);
+  }
   cudaFree(d_st);
   cudaFreeHost(h_st);
   cudaFree(d_partials);
@@ -433,9 +442,11 @@ dirac_status Engine::set_fields(int b, const double* V_dev, double ax, double ay
       to_float_kernel<<<256, 256, 0, stream>>>(V_dev, static_cast<float*>(q.V), q.n);
       ++launches;
       CUDA_TRY(cudaGetLastError());
+      if (!q.V64) CUDA_TRY(cudaMalloc(&q.V64, sizeof(double) * q.n));
     } else {
-      CUDA_TRY(cudaMemcpyAsync(q.V, V_dev, sizeof(double) * q.n, cudaMemcpyDeviceToDevice, stream));
+      q.V64 = static_cast<double*>(q.V);
     }
+    CUDA_TRY(cudaMemcpyAsync(q.V64, V_dev, sizeof(double) * q.n, cudaMemcpyDeviceToDevice, stream));
     double* mm = d_partials;   // two doubles of scratch (rewritten by every pass)
     minmax_kernel<<<1, 256, 0, stream>>>(V_dev, q.n, mm);
     ++launches;
@@ -709,6 +720,25 @@ struct dirac_ctx {
 struct dirac_batch {
   Engine e;
 };
+
+namespace dirac {
+
+dirac_status ctx_view(dirac_ctx* ctx, CtxView* v) {
+  if (!ctx) return fail(DIRAC_EINVAL, "null context");
+  const Engine& e = ctx->e;
+  const HostProblem& q = e.P[0];
+  v->nx = q.nx; v->ny = q.ny; v->dx = q.dx; v->dy = q.dy;
+  v->mass = e.mass; v->c = e.c; v->order = e.order; v->boundary = e.boundary;
+  v->V = q.has_v ? q.V64 : nullptr;
+  v->vmin = q.vmin; v->vmax = q.vmax;
+  v->ax = q.ax; v->ay = q.ay; v->shift = q.shift;
+  v->fields_set = q.fields_set;
+  v->stream = e.stream;
+  v->launches = &ctx->e.launches;
+  return DIRAC_OK;
+}
+
+}  // namespace dirac
 
 extern "C" {
 

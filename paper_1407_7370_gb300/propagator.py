@@ -28,6 +28,18 @@ def _info(c: nat.StepInfoC) -> StepInfo:
                     np.array(c.alpha[:k]), np.array(c.beta[:k]), c.kappa_max)
 
 
+@dataclasses.dataclass
+class EigResult:
+    """Result of Propagator.eigs (energies of H - shift)."""
+    values: np.ndarray       # ascending
+    bounds: np.ndarray       # Eq. 9 bounds (folded mode: bounds on lambda)
+    iterations: int
+    n_in_window: int
+    n_converged: int
+    breakdown: bool
+    vectors: object = None   # CUDA complex128 tensor (n, ny, nx, 2) of unit Ritz vectors, or None
+
+
 def _torch():
     import torch
     return torch
@@ -125,6 +137,40 @@ class Propagator:
 
     def sync(self):
         nat.check(nat.lib().dirac_sync(self._ctx))
+
+    def apply(self, psi, out=None):
+        """out = (H - shift) psi on the device (FP64); returns out."""
+        _check_psi(psi, self.ny, self.nx)
+        if out is None:
+            out = _torch().empty_like(psi)
+        _check_psi(out, self.ny, self.nx)
+        self._sync_stream()
+        nat.check(nat.lib().dirac_apply_hamiltonian(self._ctx, ctypes.c_void_p(psi.data_ptr()),
+                                                    ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def eigs(self, start, n_want: int, max_iter: int, tol: float, window=None,
+             check_every: int = 10, reorth: bool = True, fold=None, vectors: bool = False) -> EigResult:
+        """Eigenvalue mode (dirac_lanczos_eigs): Ritz values of H - shift in ``window``
+        (direct) or nearest ``fold`` (Lanczos on (H - shift - fold)^2)."""
+        _check_psi(start, self.ny, self.nx)
+        self._sync_stream()
+        lo, hi = (window if window is not None else (0.0, 0.0))
+        vals = (ctypes.c_double * n_want)()
+        bnds = (ctypes.c_double * n_want)()
+        vec_t = None
+        if vectors:
+            vec_t = _torch().empty((n_want, self.ny, self.nx, 2), dtype=start.dtype, device=start.device)
+        info = nat.EigInfoC()
+        nat.check(nat.lib().dirac_lanczos_eigs(
+            self._ctx, ctypes.c_void_p(start.data_ptr()), n_want, max_iter, check_every, float(tol),
+            float(lo), float(hi), 1 if reorth else 0, 0 if fold is None else 1,
+            0.0 if fold is None else float(fold), vals, bnds,
+            ctypes.c_void_p(vec_t.data_ptr()) if vec_t is not None else None, ctypes.byref(info)))
+        nf = info.n_found
+        return EigResult(np.array(vals[:nf]), np.array(bnds[:nf]), info.iterations,
+                         info.n_in_window, info.n_converged, bool(info.breakdown),
+                         vec_t[:nf] if vec_t is not None else None)
 
     def use_graphs(self, enable: bool = True):
         nat.check(nat.lib().dirac_use_graphs(self._ctx, 1 if enable else 0))

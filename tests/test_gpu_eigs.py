@@ -1,0 +1,237 @@
+"""Parity of the eigenvalue mode and the Hamiltonian product (CUDA path through
+the C ABI) with the CPU FP64 oracle, plus size-independent checks at the full
+2048x2048 smoothed-Coulomb workload.
+
+Tolerances: the GPU and the oracle build T_k from the same recurrence but
+round differently (sums in another order, alpha accumulated from the two
+Gram-Schmidt passes), so T_k agrees to a few ulps of ||A||; a converged Ritz
+value is well conditioned and moves by about as much.  Ritz values are
+compared to 1e-11 * ||A|| (||A|| <= ~4e4 here); folded mode squares A, so
+there the floor is u ||A|| / |lambda - sigma| (the oracle's own pin).
+"""
+import numpy as np
+import pytest
+
+from oracle import hamiltonian as ham
+from oracle import lanczos as lz
+from paper_1407_7370_gb300 import workloads as wl
+from test_oracle_hamiltonian import plane_wave_eigpair
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+C = 137.036
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1407_7370_gb300 import build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+
+
+def make(grid, V=None, A=(0.0, 0.0), shift=0.0, order=2, boundary="periodic"):
+    from paper_1407_7370_gb300 import Propagator
+    p = Propagator(grid.nx, grid.ny, grid.dx, grid.dy, order=order, boundary=boundary, m_max=4)
+    p.set_fields(None if V is None else torch.from_numpy(np.ascontiguousarray(V)).cuda(), A=A,
+                 shift=shift)
+    op = ham.Operator(grid.nx, grid.ny, grid.dx, grid.dy, order=order,
+                      boundary=ham.DIRICHLET if boundary == "dirichlet" else ham.PERIODIC,
+                      V=V, A=A, shift=shift)
+    return p, op
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def norm_a(op):
+    """An upper bound of ||H - s|| (Gershgorin on the stencil): the rounding scale."""
+    mc2 = op.mass * op.c ** 2
+    kin = op.c * (np.sqrt(2.0) * (1.5 if op.order == 4 else 1.0) / min(op.dx, op.dy)
+                  + abs(op.A[0]) + abs(op.A[1]))
+    v = 0.0 if op.V is None else np.max(np.abs(op.V))
+    return mc2 + kin + v + abs(op.shift)
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("order,boundary", [(2, "periodic"), (4, "periodic"), (2, "dirichlet"),
+                                            (4, "dirichlet")])
+def test_apply_hamiltonian_matches_oracle(order, boundary):
+    g = wl.Grid(37, 29, 0.11, 0.17)            # ragged against every tile shape
+    V = wl.random_potential(g, 3, scale=40.0)
+    p, op = make(g, V=V, A=(2.5, -1.25), shift=C * C * 0.5, order=order, boundary=boundary)
+    psi = wl.random_spinor(g, 8)
+    out = p.apply(dev(psi)).cpu().numpy()
+    ref = ham.apply(op, psi)
+    assert np.max(np.abs(out - ref)) <= 1e-14 * norm_a(op) * np.max(np.abs(psi))
+
+
+def soft_core_case(n=24, m=20, dx=0.3, z=2.0):
+    g = wl.Grid(n, m, dx, dx)
+    V = wl.soft_core(g, z)
+    start = wl.positive_energy_packet(g, p0=(0.0, 0.0)) + 1e-3 * wl.random_spinor(g, 4)
+    return g, V, start
+
+
+def test_eigs_direct_matches_oracle_fixed_iterations():
+    g, V, start = soft_core_case()
+    p, op = make(g, V=V, shift=C * C)
+    window = (-C * C, 0.0)
+    res = p.eigs(dev(start), n_want=64, max_iter=150, tol=1e-9, window=window, check_every=10)
+    ref = lz.lanczos_eigs(op, start, n_want=64, max_iter=150, tol=1e-9, window=window,
+                          check_every=10)
+    assert res.iterations == ref.iterations == 150
+    assert res.values.size == min(64, ref.values.size) and res.values.size >= 4
+    scale = 1e-11 * norm_a(op)
+    assert np.max(np.abs(res.values - ref.values[: res.values.size])) <= scale
+    assert np.all(res.bounds <= 1e-9 * np.maximum(1.0, np.abs(res.values)))
+    assert res.n_converged == ref.values.size
+
+
+def test_eigs_stops_at_the_oracles_iteration():
+    g, V, start = soft_core_case(20, 20, 0.3, 3.0)
+    p, op = make(g, V=V, shift=C * C)
+    window = (-C * C, 0.0)
+    for n_want, every in ((1, 5), (3, 7)):
+        res = p.eigs(dev(start), n_want=n_want, max_iter=400, tol=1e-10, window=window,
+                     check_every=every)
+        ref = lz.lanczos_eigs(op, start, n_want=n_want, max_iter=400, tol=1e-10, window=window,
+                              check_every=every)
+        assert res.iterations == ref.iterations < 400
+        assert res.values.size == n_want
+        assert np.max(np.abs(res.values - ref.values[:n_want])) <= 1e-11 * norm_a(op)
+
+
+def test_eigs_without_reorthogonalisation_matches_oracle():
+    g, V, start = soft_core_case(16, 18, 0.3, 2.0)
+    p, op = make(g, V=V, shift=C * C)
+    window = (-C * C, 0.0)
+    res = p.eigs(dev(start), n_want=64, max_iter=60, tol=1e-8, window=window, reorth=False)
+    ref = lz.lanczos_eigs(op, start, n_want=64, max_iter=60, tol=1e-8, window=window,
+                          reorth=False)
+    assert res.iterations == ref.iterations == 60
+    assert res.values.size == min(64, ref.values.size) >= 1
+    assert np.max(np.abs(res.values - ref.values[: res.values.size])) <= 1e-10 * norm_a(op)
+
+
+def test_eigs_folded_matches_oracle():
+    g = wl.Grid(10, 10, 0.3, 0.3)
+    V = wl.soft_core(g, 3.0)
+    p, op = make(g, V=V, shift=C * C)
+    start = wl.random_spinor(g, 5)
+    sigma = -2.0
+    res = p.eigs(dev(start), n_want=3, max_iter=200, tol=1e-9, fold=sigma, vectors=True)
+    ref = lz.lanczos_eigs(op, start, n_want=3, max_iter=200, tol=1e-9, window=None, fold=sigma,
+                          vectors=True)
+    ev = np.linalg.eigvalsh(ham.dense(op))
+    want = np.sort(ev[np.argsort(np.abs(ev - sigma))[:3]])
+    assert res.iterations == ref.iterations
+    assert res.values.size == 3
+    floor = 2.2e-16 * norm_a(op) ** 2 / np.abs(want - sigma)
+    assert np.all(np.abs(res.values - ref.values) <= 2 * floor)
+    assert np.all(np.abs(res.values - want) <= res.bounds + floor)
+    for y, yr in zip(res.vectors.cpu().numpy(), ref.vectors):
+        assert abs(abs(np.vdot(yr.reshape(-1), y.reshape(-1))) - 1.0) <= 1e-8
+
+
+def test_ritz_vectors_match_oracle_and_residual_identity():
+    g, V, start = soft_core_case(20, 16, 0.3, 2.0)
+    p, op = make(g, V=V, shift=C * C)
+    window = (-C * C, 0.0)
+    res = p.eigs(dev(start), n_want=3, max_iter=200, tol=1e-10, window=window, vectors=True)
+    ref = lz.lanczos_eigs(op, start, n_want=3, max_iter=200, tol=1e-10, window=window,
+                          vectors=True)
+    assert res.iterations == ref.iterations
+    ys = res.vectors
+    for l in range(res.values.size):
+        y = ys[l]
+        assert abs(torch.linalg.vector_norm(y).item() - 1.0) <= 1e-12
+        # Eq. 10: ||A y - theta y|| = |beta_k t_k| for a Ritz pair
+        r = torch.linalg.vector_norm(p.apply(y) - res.values[l] * y).item()
+        assert r <= res.bounds[l] + 1e-10 * norm_a(op)
+        yr = ref.vectors[l].reshape(-1)
+        gap = np.min(np.abs(np.delete(ref.all_ritz, np.argmin(np.abs(ref.all_ritz - ref.values[l])))
+                            - ref.values[l]))
+        if gap > 1e-6:   # non-degenerate: the vector is unique up to a phase
+            assert abs(abs(np.vdot(yr, y.cpu().numpy().reshape(-1))) - 1.0) <= 1e-8
+
+
+def test_eigs_breakdown_gives_exact_free_energies():
+    nx, ny, dx, dy, A = 8, 8, 0.3, 0.3, (1.5, 0.0)
+    g = wl.Grid(nx, ny, dx, dy)
+    p, op = make(g, A=A)
+    vecs, energies = [], []
+    for jx, jy, sign in ((1, 0, 1), (1, 0, -1), (2, 3, 1)):
+        psi, E = plane_wave_eigpair(nx, ny, dx, dy, jx, jy, 2, A, 0.0, sign=sign)
+        vecs.append(psi)
+        energies.append(E)
+    start = vecs[0] + 0.7 * vecs[1] + 0.4 * vecs[2]
+    res = p.eigs(dev(start), n_want=10, max_iter=50, tol=1e-10, window=(-1e9, 1e9))
+    assert res.breakdown and res.iterations == 3
+    assert np.allclose(res.values, np.sort(energies), rtol=1e-12, atol=0)
+
+
+def test_eigs_rejects_bad_arguments():
+    from paper_1407_7370_gb300._native import DiracError
+    g, V, start = soft_core_case(8, 8, 0.3, 2.0)
+    p, _ = make(g, V=V, shift=C * C)
+    s = dev(start)
+    with pytest.raises(DiracError):
+        p.eigs(s, n_want=0, max_iter=10, tol=1e-8, window=(-1.0, 0.0))
+    with pytest.raises(DiracError):
+        p.eigs(s, n_want=1, max_iter=10, tol=1e-8, window=(0.0, -1.0))
+    with pytest.raises(DiracError):
+        p.eigs(torch.zeros_like(s), n_want=1, max_iter=10, tol=1e-8, window=(-1.0, 0.0))
+
+
+@pytest.mark.slow
+def test_eigs_48_grid_matches_dense_eigh():
+    """Smoothed Coulomb Z = 20, a = 0.5 on a 48x48 grid, dx = 0.1: the eigen
+    mode's converged values against the dense spectrum of the same operator."""
+    import scipy.linalg
+    g = wl.Grid(48, 48, 0.1, 0.1)
+    V = wl.smoothed_coulomb(g, 20.0, 0.5)
+    p, op = make(g, V=V, shift=C * C)
+    x, y = g.coords()
+    start = np.zeros((48, 48, 2), complex)
+    start[..., 0] = np.exp(-(x * x + y * y) * 4.0)
+    start = start + 1e-3 * wl.random_spinor(g, 1)
+    window = (-C * C, 0.0)
+    res = p.eigs(dev(start), n_want=8, max_iter=600, tol=1e-9, window=window, check_every=10)
+    ev = scipy.linalg.eigh(ham.dense(op), eigvals_only=True, subset_by_value=window)
+    assert res.values.size >= 4
+    for v, b in zip(res.values, res.bounds):
+        assert np.min(np.abs(ev - v)) <= b + 1e-11 * norm_a(op)
+    # the lowest bound state is found
+    assert abs(res.values[0] - ev[0]) <= 1e-8 * abs(ev[0])
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("z", [20.0, 60.0])
+def test_eigs_full_size_coulomb_2048(z):
+    """2048x2048, dx = 0.02, V = -Z/sqrt(r^2 + 0.25), up to 400 iterations: the
+    converged Ritz pairs satisfy the Eq. 10 residual identity with the GPU
+    Hamiltonian, lie in the window, and are orthonormal."""
+    n = 2048
+    g = wl.Grid(n, n, 0.02, 0.02)
+    V = wl.smoothed_coulomb(g, z, 0.5)
+    p, op = make(g, V=V, shift=C * C)
+    x, y = g.coords()
+    start = np.zeros((n, n, 2), complex)
+    start[..., 0] = np.exp(-(x * x + y * y) * z)
+    start = start + 1e-3 * wl.random_spinor(g, 2) * np.exp(-(x * x + y * y))[..., None]
+    res = p.eigs(dev(start), n_want=8, max_iter=400, tol=1e-8, window=(-C * C, 0.0),
+                 vectors=True)
+    assert res.values.size >= 1
+    Y = res.vectors.reshape(res.values.size, -1)
+    gram = (Y.conj() @ Y.T).cpu().numpy()
+    assert np.max(np.abs(gram - np.eye(res.values.size))) <= 1e-8
+    for l in range(res.values.size):
+        yl = res.vectors[l]
+        r = torch.linalg.vector_norm(p.apply(yl) - res.values[l] * yl).item()
+        assert r <= res.bounds[l] * (1 + 1e-6) + 1e-10 * norm_a(op)
+        assert -C * C < res.values[l] < 0.0
+    # the ground state sits below the top of the smoothed well's depth
+    assert res.values[0] > -z / 0.5 - 1e-6
