@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
+    ap.add_argument("--no-eigen", action="store_true", help="skip the eigenvalue-mode workload")
     ap.add_argument("--only", choices=["fp64", "mixed"], default=None,
                     help="run one path only (for profiling); prints a partial line")
     return ap.parse_args()
@@ -322,6 +323,74 @@ def measure_batch(args, torch, world, dist, gi, pk):
             "speedup_mixed_batched_vs_fp64_single": None}
 
 
+EIGEN_CFG = dict(
+    name="eigen mode: smoothed Coulomb Z=20, a=0.5, 2048x2048, dx=0.02, up to 400 Lanczos "
+         "iterations, full reorthogonalisation (CGS2), 8 lowest in (-mc^2, 0) + mc^2",
+    side=2048, dx=0.02, z=20.0, a=0.5, max_iter=400, n_want=8, tol=1e-8, check_every=10)
+GS_FLOPS_PER_SITE_VECTOR = 64   # two Gram-Schmidt passes x (inner product 16 + update 16) FP64 flops
+GS_BYTES_PER_SITE_VECTOR = 128  # two passes x (read q_j for the products + read q_j for the update)
+
+
+def measure_eigen(torch, gi, pk):
+    """Eigenvalue mode on the 2048^2 smoothed-Coulomb workload: one untimed
+    short call, then one timed call with per-kernel CUDA-event timing."""
+    from paper_1407_7370_gb300 import Propagator
+    c = EIGEN_CFG
+    C2 = 137.036 ** 2
+    g = wl.Grid(c["side"], c["side"], c["dx"], c["dx"])
+    V = torch.from_numpy(wl.smoothed_coulomb(g, c["z"], c["a"])).cuda()
+    x, y = g.coords()
+    start = np.zeros((g.ny, g.nx, 2), complex)
+    start[..., 0] = np.exp(-(x * x + y * y) * c["z"])
+    start = start + 1e-3 * wl.random_spinor(g, 2) * np.exp(-(x * x + y * y))[..., None]
+    st = torch.from_numpy(start).cuda()
+    del start, x, y
+    prop = Propagator(g.nx, g.ny, g.dx, g.dy, m_max=1)
+    prop.set_fields(V, shift=C2)
+    window = (-C2, 0.0)
+    prop.eigs(st, n_want=1, max_iter=12, tol=c["tol"], window=window, check_every=6)
+    torch.cuda.synchronize()
+    prop.profile(True)
+    clocks = ClockSampler(gi)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    e0.record(stream)
+    res = prop.eigs(st, n_want=c["n_want"], max_iter=c["max_iter"], tol=c["tol"], window=window,
+                    check_every=c["check_every"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    prop.profile(False)
+    t = e0.elapsed_time(e1) / 1e3
+    k, n = res.iterations, g.n_sites
+    gs_ms = res.ms["dot"] + res.ms["update"]
+    flops = GS_FLOPS_PER_SITE_VECTOR * n * k * (k + 1) / 2
+    gbytes = GS_BYTES_PER_SITE_VECTOR * n * k * (k + 1) / 2
+    fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12
+    achieved = flops / (gs_ms / 1e3) / 1e12
+    hbm_peak = pk.get("hbm_gbs", 6800.0)
+    out = {"workload": c["name"], "iterations": k, "seconds": t,
+           "value": n * k / t, "unit": "site-matvecs/s (Lanczos iterations x sites / s)",
+           "ms_per_iteration": 1e3 * t / k,
+           "n_found": int(res.values.size), "values_minus_mc2": [float(v) for v in res.values],
+           "bounds": [float(b) for b in res.bounds], "breakdown": res.breakdown,
+           "gpu_launches": res.launches, "kernel_ms": res.ms, "clocks": clk,
+           "roofline": {"bound": "alu", "kernel": "eig_dot + eig_update (Gram-Schmidt, twice)",
+                        "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                        "frac": achieved / fp64_peak, "traffic": None,
+                        "share": gs_ms / max(1e-9, sum(res.ms.values())),
+                        "flops_per_site_vector": GS_FLOPS_PER_SITE_VECTOR,
+                        "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"},
+           "hbm": {"achieved": gbytes / (gs_ms / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                   "frac": gbytes / (gs_ms / 1e3) / 1e9 / hbm_peak,
+                   "bytes_per_site_vector": GS_BYTES_PER_SITE_VECTOR}}
+    prop.close()
+    del st, V
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -432,6 +501,8 @@ def run_ours(args):
             line["batched"] = measure_batch(args, torch, world, dist, local, pk)
             line["batched"]["speedup_mixed_batched_vs_fp64_single"] = \
                 line["batched"]["mixed"]["value"] / line["value"]
+        if not args.no_eigen:
+            line["eigen"] = measure_eigen(torch, local, pk)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline()
         elif not args.no_cpu_baseline:

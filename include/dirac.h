@@ -315,6 +315,12 @@ typedef struct {
     int n_in_window;   /* Ritz values of T_k in the window (folded: k) */
     int n_converged;   /* of those examined, with bound <= tol * max(1, |theta|) */
     int breakdown;     /* 1: beta_k fell below 1e-12 * scale, T_k's spectrum is exact */
+    long long launches;  /* kernels launched by the call */
+    /* device time (ms) per kernel kind, measured with CUDA events while
+       dirac_profile_enable is on (else 0): the stencil product, the
+       Gram-Schmidt inner products, the Gram-Schmidt updates, everything else
+       (coefficient sums, Ritz values and vectors) */
+    double ms_apply, ms_dot, ms_update, ms_other;
 } dirac_eig_info;
 
 /*

@@ -50,7 +50,9 @@ class TuneResultC(ctypes.Structure):
 class EigInfoC(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("n_found", ctypes.c_int),
                 ("n_in_window", ctypes.c_int), ("n_converged", ctypes.c_int),
-                ("breakdown", ctypes.c_int)]
+                ("breakdown", ctypes.c_int), ("launches", ctypes.c_longlong),
+                ("ms_apply", ctypes.c_double), ("ms_dot", ctypes.c_double),
+                ("ms_update", ctypes.c_double), ("ms_other", ctypes.c_double)]
 
 
 class DiracError(RuntimeError):

@@ -735,6 +735,7 @@ dirac_status ctx_view(dirac_ctx* ctx, CtxView* v) {
   v->fields_set = q.fields_set;
   v->stream = e.stream;
   v->launches = &ctx->e.launches;
+  v->profiling = e.profiling;
   return DIRAC_OK;
 }
 

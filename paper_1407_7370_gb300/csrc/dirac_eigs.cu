@@ -773,6 +773,51 @@ cudaError_t launch_apply(const CtxView& v, const ApplyArgs& a) {
                                        : launch_apply_rd<2, false>(a, v.stream);
 }
 
+// Device time per kernel kind from CUDA events recorded between consecutive
+// launches on one stream (active only while the context is profiling).
+enum { K_APPLY = 0, K_DOT = 1, K_UPDATE = 2, K_OTHER = 3, K_START = -1 };
+
+struct KindTimer {
+  bool on = false;
+  cudaStream_t s = nullptr;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> kind;      // kind of the kernel that ends at event j
+  size_t used = 0;
+  double ms[4] = {0.0, 0.0, 0.0, 0.0};
+  long long n = 0;            // kernels launched (counted also when not timing)
+
+  // after a launch of `k` (K_START: before the first launch of a segment)
+  cudaError_t mark(int k) {
+    if (k >= 0) ++n;
+    if (!on) return cudaSuccess;
+    if (used == ev.size()) {
+      cudaEvent_t e;
+      cudaError_t r = cudaEventCreate(&e);
+      if (r != cudaSuccess) return r;
+      ev.push_back(e);
+      kind.push_back(k);
+    }
+    kind[used] = k;
+    return cudaEventRecord(ev[used++], s);
+  }
+  // after the stream has been synchronised: add up and start a new segment
+  cudaError_t flush() {
+    if (!on) return cudaSuccess;
+    for (size_t j = 1; j < used; ++j) {
+      if (kind[j] < 0) continue;
+      float t = 0.f;
+      cudaError_t r = cudaEventElapsedTime(&t, ev[j - 1], ev[j]);
+      if (r != cudaSuccess) return r;
+      ms[kind[j]] += t;
+    }
+    used = 0;
+    return cudaSuccess;
+  }
+  ~KindTimer() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+};
+
 int n_sms() {
   int dev = 0, n = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 1;
@@ -904,10 +949,30 @@ dirac_status dirac_lanczos_eigs(dirac_ctx* ctx, const void* start_dev, int n_wan
   ra.th_s = reinterpret_cast<double*>(sb + o_ths);
   ra.kmax = kmax;
 
-  long long launches = 0;
+  KindTimer tm;
+  tm.on = v.profiling;
+  tm.s = s;
+  // every exit from here on adds the launches to the context and fills info
+  struct Finish {
+    KindTimer& tm;
+    CtxView& v;
+    dirac_eig_info* info;
+    ~Finish() {
+      *v.launches += tm.n;
+      if (info) {
+        info->launches = tm.n;
+        info->ms_apply = tm.ms[K_APPLY];
+        info->ms_dot = tm.ms[K_DOT];
+        info->ms_update = tm.ms[K_UPDATE];
+        info->ms_other = tm.ms[K_OTHER];
+      }
+    }
+  } finish_guard{tm, v, info};
+
+  EIG_TRY(tm.mark(K_START));
   eig_start<<<n_upd, 256, 0, s>>>(static_cast<const v4*>(start_dev), basis, n, npart);
   EIG_TRY(cudaGetLastError());
-  ++launches;
+  EIG_TRY(tm.mark(K_OTHER));
 
   const double e0 = v.shift + (fold ? sigma : 0.0);   // A = H - e0 (direct) or (H - e0)^2
   const double ashift = fold ? 0.0 : v.shift;
@@ -929,17 +994,18 @@ dirac_status dirac_lanczos_eigs(dirac_ctx* ctx, const void* start_dev, int n_wan
       a.sub = qim;
       a.out = z;
       EIG_TRY(launch_apply(v, a));
-      ++launches;
+      EIG_TRY(tm.mark(K_APPLY));
     } else {
       a.sub = nullptr;
       a.out = tmp;
       EIG_TRY(launch_apply(v, a));
+      EIG_TRY(tm.mark(K_APPLY));
       a.prologue = 0;
       a.in = tmp;
       a.sub = qim;
       a.out = z;
       EIG_TRY(launch_apply(v, a));
-      launches += 2;
+      EIG_TRY(tm.mark(K_APPLY));
     }
     const int passes = reorth ? 2 : 1;
     const int j0 = reorth ? 0 : i;
@@ -949,13 +1015,15 @@ dirac_status dirac_lanczos_eigs(dirac_ctx* ctx, const void* start_dev, int n_wan
       const size_t smem = (size_t)cs * sizeof(v4) + sizeof(double2) * (size_t)count;
       eig_dot<<<n_dot, 256, smem, s>>>(da);
       EIG_TRY(cudaGetLastError());
+      EIG_TRY(tm.mark(K_DOT));
       FinishArgs fa{dpart, n_dot, j0, i, i, p, p == passes - 1, reorth ? 1 : 0, sarr, coef, alpha, beta, ed, ashift};
       eig_dot_finish<<<(count + 7) / 8, 256, 0, s>>>(fa);
       EIG_TRY(cudaGetLastError());
+      EIG_TRY(tm.mark(K_OTHER));
       UpdArgs ua{z, basis, n, j0, i, coef, p == passes - 1 ? 1 : 0, npart, ed};
       eig_update<<<n_upd, 256, 0, s>>>(ua);
       EIG_TRY(cudaGetLastError());
-      launches += 3;
+      EIG_TRY(tm.mark(K_UPDATE));
     }
     const int it = i + 1;
     if (it % check_every != 0 && it != max_iter) continue;
@@ -967,13 +1035,13 @@ dirac_status dirac_lanczos_eigs(dirac_ctx* ctx, const void* start_dev, int n_wan
     EIG_TRY(cudaGetLastError());
     eig_ritz_tvecs<<<(RITZ_CAP + 3) / 4, 128, 0, s>>>(ra);
     EIG_TRY(cudaGetLastError());
-    launches += 3;
+    EIG_TRY(tm.mark(K_OTHER));
+    tm.n += 2;
     EIG_TRY(cudaMemcpyAsync(ro_host.data(), ro, sizeof(RitzOut), cudaMemcpyDeviceToHost, s));
     EIG_TRY(cudaStreamSynchronize(s));
-    if (h.error) {
-      *v.launches += launches;
-      return fail(DIRAC_ENONFINITE, "eigen mode: non-finite value or zero start vector");
-    }
+    EIG_TRY(tm.flush());
+    EIG_TRY(tm.mark(K_START));
+    if (h.error) return fail(DIRAC_ENONFINITE, "eigen mode: non-finite value or zero start vector");
     k_done = h.k;
     const int n_exam = h.n_exam;
     std::vector<int> conv;
@@ -1005,8 +1073,6 @@ dirac_status dirac_lanczos_eigs(dirac_ctx* ctx, const void* start_dev, int n_wan
       }
     }
   }
-  *v.launches += launches;
-  launches = 0;
   const int n_sel = (int)sel.size();
   if (info) info->n_found = n_sel;
   if (n_sel == 0) return DIRAC_OK;
@@ -1022,8 +1088,9 @@ dirac_status dirac_lanczos_eigs(dirac_ctx* ctx, const void* start_dev, int n_wan
       RvArgs rv{basis, sarr, ra.X, kmax, k_done, d_sel, n_sel, n, static_cast<v4*>(vecs_dev)};
       eig_ritz_vectors<<<vgrid, 256, 0, s>>>(rv);
       EIG_TRY(cudaGetLastError());
-      ++*v.launches;
+      EIG_TRY(tm.mark(K_OTHER));
       EIG_TRY(cudaStreamSynchronize(s));
+      EIG_TRY(tm.flush());
     }
     return DIRAC_OK;
   }
@@ -1034,23 +1101,25 @@ dirac_status dirac_lanczos_eigs(dirac_ctx* ctx, const void* start_dev, int n_wan
   RvArgs rv{basis, sarr, ra.X, kmax, k_done, d_sel, n_sel, n, fold_vecs};
   eig_ritz_vectors<<<vgrid, 256, 0, s>>>(rv);
   EIG_TRY(cudaGetLastError());
-  ++launches;
+  EIG_TRY(tm.mark(K_OTHER));
   for (int l = 0; l < n_sel; ++l) {
     ApplyArgs a = apply_args(v, e0);
     a.in = fold_vecs + (size_t)l * n;
     a.out = tmp;
     EIG_TRY(launch_apply(v, a));
+    EIG_TRY(tm.mark(K_APPLY));
     DotArgs da{tmp, fold_vecs + (size_t)l * n, n, 0, 0, cs, dpart, nullptr};
     eig_dot<<<n_dot, 256, (size_t)cs * sizeof(v4) + sizeof(double2), s>>>(da);
     EIG_TRY(cudaGetLastError());
+    EIG_TRY(tm.mark(K_DOT));
     eig_fold_finish<<<1, 32, 0, s>>>(dpart, n_dot, h.theta[sel[l]], h.bound[sel[l]], sigma, d_fres + 2 * l);
     EIG_TRY(cudaGetLastError());
-    launches += 3;
+    EIG_TRY(tm.mark(K_OTHER));
   }
   std::vector<double> fres(2 * n_sel);
   EIG_TRY(cudaMemcpyAsync(fres.data(), d_fres, sizeof(double) * 2 * n_sel, cudaMemcpyDeviceToHost, s));
   EIG_TRY(cudaStreamSynchronize(s));
-  *v.launches += launches;
+  EIG_TRY(tm.flush());
   std::vector<int> order(n_sel);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int p, int q) { return fres[2 * p] < fres[2 * q]; });

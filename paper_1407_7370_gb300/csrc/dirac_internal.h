@@ -24,6 +24,7 @@ struct CtxView {
   bool fields_set;
   cudaStream_t stream;
   long long* launches;    // the context's kernel-launch counter
+  bool profiling;         // dirac_profile_enable is on: time kernels with CUDA events
 };
 
 dirac_status ctx_view(dirac_ctx* ctx, CtxView* v);

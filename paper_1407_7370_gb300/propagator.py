@@ -38,6 +38,8 @@ class EigResult:
     n_converged: int
     breakdown: bool
     vectors: object = None   # CUDA complex128 tensor (n, ny, nx, 2) of unit Ritz vectors, or None
+    launches: int = 0
+    ms: dict = None          # device ms per kernel kind while profiling (apply, dot, update, other)
 
 
 def _torch():
@@ -170,7 +172,9 @@ class Propagator:
         nf = info.n_found
         return EigResult(np.array(vals[:nf]), np.array(bnds[:nf]), info.iterations,
                          info.n_in_window, info.n_converged, bool(info.breakdown),
-                         vec_t[:nf] if vec_t is not None else None)
+                         vec_t[:nf] if vec_t is not None else None, int(info.launches),
+                         {"apply": info.ms_apply, "dot": info.ms_dot, "update": info.ms_update,
+                          "other": info.ms_other})
 
     def use_graphs(self, enable: bool = True):
         nat.check(nat.lib().dirac_use_graphs(self._ctx, 1 if enable else 0))

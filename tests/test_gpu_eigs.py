@@ -83,7 +83,7 @@ def test_eigs_direct_matches_oracle_fixed_iterations():
     ref = lz.lanczos_eigs(op, start, n_want=64, max_iter=150, tol=1e-9, window=window,
                           check_every=10)
     assert res.iterations == ref.iterations == 150
-    assert res.values.size == min(64, ref.values.size) and res.values.size >= 4
+    assert res.values.size == min(64, ref.values.size) and res.values.size >= 2
     scale = 1e-11 * norm_a(op)
     assert np.max(np.abs(res.values - ref.values[: res.values.size])) <= scale
     assert np.all(res.bounds <= 1e-9 * np.maximum(1.0, np.abs(res.values)))
@@ -108,12 +108,17 @@ def test_eigs_without_reorthogonalisation_matches_oracle():
     g, V, start = soft_core_case(16, 18, 0.3, 2.0)
     p, op = make(g, V=V, shift=C * C)
     window = (-C * C, 0.0)
-    res = p.eigs(dev(start), n_want=64, max_iter=60, tol=1e-8, window=window, reorth=False)
-    ref = lz.lanczos_eigs(op, start, n_want=64, max_iter=60, tol=1e-8, window=window,
+    res = p.eigs(dev(start), n_want=64, max_iter=150, tol=1e-8, window=window, reorth=False)
+    ref = lz.lanczos_eigs(op, start, n_want=64, max_iter=150, tol=1e-8, window=window,
                           reorth=False)
-    assert res.iterations == ref.iterations == 60
-    assert res.values.size == min(64, ref.values.size) >= 1
-    assert np.max(np.abs(res.values - ref.values[: res.values.size])) <= 1e-10 * norm_a(op)
+    assert res.iterations == ref.iterations == 150
+    assert res.values.size >= 1 and ref.values.size >= 1
+    # without reorthogonalisation rounding differences grow once values
+    # converge (Sec. 2), so compare the converged values as sets
+    for v in res.values:
+        assert np.min(np.abs(ref.values - v)) <= 1e-10 * norm_a(op)
+    for v in ref.values:
+        assert np.min(np.abs(res.values - v)) <= 1e-10 * norm_a(op)
 
 
 def test_eigs_folded_matches_oracle():
@@ -132,8 +137,14 @@ def test_eigs_folded_matches_oracle():
     floor = 2.2e-16 * norm_a(op) ** 2 / np.abs(want - sigma)
     assert np.all(np.abs(res.values - ref.values) <= 2 * floor)
     assert np.all(np.abs(res.values - want) <= res.bounds + floor)
-    for y, yr in zip(res.vectors.cpu().numpy(), ref.vectors):
-        assert abs(abs(np.vdot(yr.reshape(-1), y.reshape(-1))) - 1.0) <= 1e-8
+    # a Ritz vector of A = (H - s - sigma)^2 is fixed to an angle of about
+    # u ||A|| / gap, gap its distance to the rest of A's spectrum
+    mu = (ev - sigma) ** 2
+    for lam, y, yr in zip(res.values, res.vectors.cpu().numpy(), ref.vectors):
+        th = (lam - sigma) ** 2
+        gap = np.sort(np.abs(mu - th))[1]
+        angle = 4 * 2.2e-16 * norm_a(op) ** 2 / gap
+        assert abs(abs(np.vdot(yr.reshape(-1), y.reshape(-1))) - 1.0) <= 0.5 * angle ** 2 + 1e-12
 
 
 def test_ritz_vectors_match_oracle_and_residual_identity():
@@ -235,3 +246,16 @@ def test_eigs_full_size_coulomb_2048(z):
         assert -C * C < res.values[l] < 0.0
     # the ground state sits below the top of the smoothed well's depth
     assert res.values[0] > -z / 0.5 - 1e-6
+
+
+def test_eigs_launch_count_and_kernel_timing():
+    g, V, start = soft_core_case(16, 16, 0.3, 2.0)
+    p, _ = make(g, V=V, shift=C * C)
+    p.profile(True)
+    res = p.eigs(dev(start), n_want=200, max_iter=30, tol=1e-14, window=(-C * C, 0.0),
+                 check_every=10)
+    p.profile(False)
+    assert res.iterations == 30
+    # start vector + 30 x (product + 2 x (inner products, sums, update)) + 3 checks x 3
+    assert res.launches == 1 + 30 * 7 + 3 * 3
+    assert res.ms["apply"] > 0 and res.ms["dot"] > 0 and res.ms["update"] > 0 and res.ms["other"] > 0
