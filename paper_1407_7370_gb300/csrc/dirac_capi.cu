@@ -134,11 +134,12 @@ bool pdl_enabled() {
 // while the previous kernel in the stream finishes; it waits for it (and sees
 // its writes) at its griddepcontrol.wait.
 template <class... KArgs, class... Args>
-cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream_t s, Args&&... args) {
+cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -154,22 +155,31 @@ struct LaunchShape {
   int cta_cap;       // 0: as many CTAs per SM as fit; else at most this many
 };
 
-// Persistent launch: at most (resident CTAs) CTAs, each taking an equal
-// contiguous chunk of the tile list.
+// Persistent launch: as many CTAs as are resident at once (at most one per
+// tile), each taking a contiguous chunk of the tile list whose size differs
+// from the others' by at most one tile.
 template <class S, int R, int TH, bool D, bool V>
 cudaError_t launch_pass_t(LaunchParams p, const LaunchShape& ls, cudaStream_t s) {
   static int occ = 0;
-  constexpr int NT = 32 * (TH / RPT);
+  constexpr int NT = sub_workers<S>() * 32 * (TH / RPT);
+  constexpr size_t smem = dyn_smem_bytes<S, R, TH, sub_workers<S>()>();
   if (occ == 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lanczos_pass<S, R, TH, D, V>, NT, 0);
+    cudaError_t e = cudaSuccess;
+    if (smem > 0) {
+      e = cudaFuncSetAttribute(lanczos_pass<S, R, TH, D, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lanczos_pass<S, R, TH, D, V>, NT, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
   }
   const int per_sm = ls.cta_cap > 0 ? std::min(occ, ls.cta_cap) : occ;
   const int slots = std::max(1, ls.n_sm * per_sm);
-  p.tiles_per_cta = (p.total_tiles + slots - 1) / slots;
-  const int grid = std::max(1, (p.total_tiles + p.tiles_per_cta - 1) / p.tiles_per_cta);
-  return launch_pdl(lanczos_pass<S, R, TH, D, V>, grid, NT, s, p);
+  const int grid = std::max(1, std::min(p.total_tiles, slots));
+  p.chunk_q = p.total_tiles / grid;
+  p.chunk_r = p.total_tiles % grid;
+  return launch_pdl(lanczos_pass<S, R, TH, D, V>, grid, NT, smem, s, p);
 }
 
 template <class S, int TH>
@@ -200,8 +210,8 @@ int redo_budget(int precision, int m) { return precision == DIRAC_FP64 ? 2 : 2 +
 double kappa_redo(int precision) { return precision == DIRAC_FP64 ? 1e12 : 1e6; }
 
 cudaError_t launch_recombine(int precision, const RecombParams& rp, int grid, cudaStream_t s) {
-  if (precision == DIRAC_FP64) return launch_pdl(recombine<false>, grid, 256, s, rp);
-  return launch_pdl(recombine<true>, grid, 256, s, rp);
+  if (precision == DIRAC_FP64) return launch_pdl(recombine<false>, grid, 256, 0, s, rp);
+  return launch_pdl(recombine<true>, grid, 256, 0, s, rp);
 }
 
 __global__ void to_float_kernel(const double* in, float* out, long long n) {

@@ -22,12 +22,15 @@
 // and beta_{i-1} is taken from the measured norm of the next vector rather
 // than from s2, so the tridiagonal T of Fig. 1 is reproduced to rounding.
 //
-// Work split: the tiles of all problems form one list; persistent CTA c takes
-// the contiguous chunk [c T, (c+1) T).  Per problem it touches, a CTA writes
-// one partial (P, Y, X) into slot c - (first CTA of that problem) and adds
-// its tile count to the problem's ticket; the CTA that completes a problem
-// sums that problem's slots in a fixed order (deterministic, no
-// floating-point atomics) and updates its scalars.
+// Work split: the tiles of all problems form one list of T tiles; persistent
+// CTA c of G takes a contiguous chunk of T / G or T / G + 1 tiles.  A CTA may hold SUB independent tile workers (groups
+// of warps with their own tile buffer and named barrier) that take the
+// chunk's tiles in turn, so that one CTA per SM still overlaps one worker's
+// loads with another's arithmetic.  Per problem it touches, a CTA writes one
+// partial (P, Y, X) into slot c - (first CTA of that problem) and adds its
+// tile count to the problem's ticket; the CTA that completes a problem sums
+// that problem's slots in a fixed order (deterministic, no floating-point
+// atomics) and updates its scalars.
 //
 // exp(-i T dt) e_1 (Sec. 4) is evaluated on one warp by a Chebyshev expansion
 // over an a-priori spectral interval of H (Jacobi-Anger coefficients computed
@@ -132,7 +135,8 @@ struct LaunchParams {
   DevState* states;         // one per problem, same order
   const FieldStep* fields;  // fields[step * fstride + problem]
   int fstride;              // 0: one FieldStep per problem for every step
-  int nprob, total_tiles, tiles_per_cta;
+  int nprob, total_tiles;
+  int chunk_q, chunk_r;     // tiles per CTA: q + 1 for the first r CTAs, then q
   int pass, m, probe;
   double mcc, dt, tol;
   const int* step;          // step counter of the running call (index into fields)
@@ -357,29 +361,66 @@ __device__ void finish_pass(const LaunchParams& lp, const Problem* pr, int i, do
 // cross-shaped halo of q^_i are formed in shared memory from y^_{i-1} and
 // q^_{i-1}.
 // ---------------------------------------------------------------------------
-template <class S, int TH>
-constexpr int min_blocks() { return sizeof(S) == sizeof(float) ? (TH == 32 ? 4 : 8) : 2; }
+template <class S, int TH, int SUB>
+__host__ __device__ constexpr int min_blocks() { return sizeof(S) == sizeof(float) ? (TH == 32 ? 4 : 8) : (SUB == 2 ? 1 : 2); }
+
+// tile workers per CTA: two on the FP64 path (one CTA per SM), one otherwise
+template <class S>
+__host__ __device__ constexpr int sub_workers() { return sizeof(S) == sizeof(double) ? 2 : 1; }
+
+// shared memory of one tile worker: the tile of q^_i with its halo
+template <class S, int R, int TH>
+__host__ __device__ constexpr size_t tile_bytes() { return sizeof(S) * 4 * (TH + 2 * R) * (TILE_W + 2 * R); }
+
+// Chunks of the tile list: CTA c takes q + 1 tiles if c < r, else q (q = T / G,
+// r = T % G), starting at c q + min(c, r).  The CTA whose chunk holds tile t:
+__device__ __forceinline__ int cta_of_tile(int t, int q, int r) {
+  const int big = r * (q + 1);
+  return t < big ? t / (q + 1) : r + (t - big) / q;
+}
+
+// shared memory of the tile workers: a static array for one worker, the
+// dynamic allocation for several (more than the 48 KiB of static memory)
+template <class S, int R, int TH, int SUB>
+__host__ __device__ constexpr size_t dyn_smem_bytes() { return SUB == 1 ? 0 : SUB * tile_bytes<S, R, TH>(); }
 
 template <class S, int R, int TH, bool DIRI, bool HAS_V>
-__global__ void __launch_bounds__(32 * (TH / RPT), (min_blocks<S, TH>()))
+__global__ void __launch_bounds__(sub_workers<S>() * 32 * (TH / RPT), (min_blocks<S, TH, sub_workers<S>()>()))
 lanczos_pass(const __grid_constant__ LaunchParams lp) {
   using T4 = typename Vec4<S>::T;           // storage of y^ (and of q^ on the mixed path)
-  constexpr int NG = TH / RPT;              // row groups = warps
-  constexpr int NT = 32 * NG;               // threads
+  constexpr int SUB = sub_workers<S>();     // tile workers
+  constexpr int NG = TH / RPT;              // row groups = warps of a worker
+  constexpr int NTS = 32 * NG;              // threads of a worker
+  constexpr int NT = SUB * NTS;             // threads
+  constexpr int NW = SUB * NG;              // warps
   constexpr int W = TILE_W + 2 * R;
-  __shared__ __align__(32) S tile[TH + 2 * R][W][4];
-  __shared__ double red[NG][3];
+  extern __shared__ __align__(32) unsigned char dyn_smem[];
+  __shared__ double red[NW][3];
   __shared__ int last_flag;
   // programmatic dependent launch: nothing the previous kernel wrote is read
   // before this point
   asm volatile("griddepcontrol.wait;" ::: "memory");
 
-  const int t_begin = blockIdx.x * lp.tiles_per_cta;
-  const int t_end = min(t_begin + lp.tiles_per_cta, lp.total_tiles);
-  const int tx = threadIdx.x & 31, tg = threadIdx.x >> 5;
-  const int warp = tg, lane = tx;
+  const int cq = lp.chunk_q, cr = lp.chunk_r;
+  const int t_begin = blockIdx.x * cq + min((int)blockIdx.x, cr);
+  const int t_end = t_begin + cq + ((int)blockIdx.x < cr ? 1 : 0);
+  const int sub = SUB == 1 ? 0 : (int)threadIdx.x / NTS;   // this thread's worker
+  const int ltid = (int)threadIdx.x - sub * NTS;
+  const int tx = ltid & 31, tg = ltid >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int step = *lp.step;
   constexpr bool F32 = sizeof(S) == sizeof(float);
+  __shared__ __align__(32) S tile_s[SUB == 1 ? TH + 2 * R : 1][W][4];
+  S(*const tile)[W][4] = SUB == 1 ? &tile_s[0]
+                                  : reinterpret_cast<S(*)[W][4]>(dyn_smem + sub * tile_bytes<S, R, TH>());
+  // barrier of this worker's threads (the whole CTA when there is one worker)
+  auto sub_sync = [&]() {
+    if constexpr (SUB == 1) {
+      __syncthreads();
+    } else {
+      asm volatile("bar.sync %0, %1;" ::"r"(1 + sub), "r"(NTS) : "memory");
+    }
+  };
 
   // problem of the first tile (problems are sorted by tile_begin)
   int b = 0;
@@ -452,8 +493,8 @@ lanczos_pass(const __grid_constant__ LaunchParams lp) {
     };
 
     S accP = S(0), accY = S(0), accX = S(0);
-    for (; t < seg_end; ++t) {
-      const int lt = t - pr->tile_begin;
+    for (int tt = t + sub; tt < seg_end; tt += SUB) {
+      const int lt = tt - pr->tile_begin;
       const int x0 = (lt % pr->tiles_x) * TILE_W;
       const int y0 = (lt / pr->tiles_x) * TH;
       S qprev[RPT][4];
@@ -463,7 +504,7 @@ lanczos_pass(const __grid_constant__ LaunchParams lp) {
         form(x0 + tx, y0 + r, r + R, tx + R, qprev[k]);
       }
       constexpr int NH_ROW = 2 * R * TILE_W, NH = NH_ROW + 2 * R * TH;
-      for (int h = threadIdx.x; h < NH; h += NT) {
+      for (int h = ltid; h < NH; h += NTS) {
         int row, col;
         if (h < NH_ROW) {               // rows above / below
           const int r = h / TILE_W;
@@ -478,7 +519,7 @@ lanczos_pass(const __grid_constant__ LaunchParams lp) {
         S dummy[4];
         form(x0 + col - R, y0 + row - R, row, col, dummy);
       }
-      __syncthreads();
+      sub_sync();
 
 #pragma unroll
       for (int k = 0; k < RPT; ++k) {
@@ -543,8 +584,9 @@ lanczos_pass(const __grid_constant__ LaunchParams lp) {
           }
         }
       }
-      __syncthreads();   // the tile buffer is reused next
+      sub_sync();   // the tile buffer is reused next
     }
+    t = seg_end;
 
     // this CTA's share of the problem: thread -> warp in S, warps -> CTA in
     // double, one partial per (problem, CTA) slot, then the ticket
@@ -555,15 +597,15 @@ lanczos_pass(const __grid_constant__ LaunchParams lp) {
     __syncthreads();
     if (warp == 0) {
       double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-      if (lane < NG) { s0 = red[lane][0]; s1 = red[lane][1]; s2 = red[lane][2]; }
+      if (lane < NW) { s0 = red[lane][0]; s1 = red[lane][1]; s2 = red[lane][2]; }
 #pragma unroll
-      for (int o = 4; o > 0; o >>= 1) {   // NG <= 8 warps
+      for (int o = 8; o > 0; o >>= 1) {   // NW <= 16 warps
         s0 += __shfl_xor_sync(0xffffffffu, s0, o);
         s1 += __shfl_xor_sync(0xffffffffu, s1, o);
         s2 += __shfl_xor_sync(0xffffffffu, s2, o);
       }
       if (lane == 0) {
-        const int slot = blockIdx.x - pr->tile_begin / lp.tiles_per_cta;
+        const int slot = blockIdx.x - cta_of_tile(pr->tile_begin, cq, cr);
         pr->partials[3 * slot + 0] = s0;
         pr->partials[3 * slot + 1] = s1;
         pr->partials[3 * slot + 2] = s2;
@@ -574,12 +616,24 @@ lanczos_pass(const __grid_constant__ LaunchParams lp) {
       }
     }
     __syncthreads();
-    if (last_flag && warp == 0) {
-      // the problem is complete: sum its slots in a fixed order
-      const int cta_lo = pr->tile_begin / lp.tiles_per_cta;
-      const int nslots = (pr->tile_begin + pr->ntiles - 1) / lp.tiles_per_cta - cta_lo + 1;
+    if (last_flag) {
+      // the problem is complete: the whole CTA sums its slots in a fixed
+      // order (thread-strided, the warp tree, then the warps in turn), the
+      // loads batched so that their L2 round trips overlap
+      const int cta_lo = cta_of_tile(pr->tile_begin, cq, cr);
+      const int nslots = cta_of_tile(pr->tile_begin + pr->ntiles - 1, cq, cr) - cta_lo + 1;
       double t0 = 0.0, t1 = 0.0, t2 = 0.0;
-      for (int s = lane; s < nslots; s += 32) {
+      int s = threadIdx.x;
+      for (; s + NT < nslots; s += 2 * NT) {
+        const double* p0 = pr->partials + 3 * s;
+        const double* p1 = p0 + 3 * NT;
+        const double a0 = __ldcg(p0), a1 = __ldcg(p0 + 1), a2 = __ldcg(p0 + 2);
+        const double c0 = __ldcg(p1), c1 = __ldcg(p1 + 1), c2 = __ldcg(p1 + 2);
+        t0 += a0 + c0;
+        t1 += a1 + c1;
+        t2 += a2 + c2;
+      }
+      for (; s < nslots; s += NT) {
         t0 += __ldcg(pr->partials + 3 * s + 0);
         t1 += __ldcg(pr->partials + 3 * s + 1);
         t2 += __ldcg(pr->partials + 3 * s + 2);
@@ -587,8 +641,15 @@ lanczos_pass(const __grid_constant__ LaunchParams lp) {
       t0 = warp_sum(t0);
       t1 = warp_sum(t1);
       t2 = warp_sum(t2);
-      if (lane == 0) pr->st->counter = 0u;
-      finish_pass(lp, pr, i, t0, t1, t2);
+      if (lane == 0) { red[warp][0] = t0; red[warp][1] = t1; red[warp][2] = t2; }
+      __syncthreads();
+      if (warp == 0) {
+        t0 = red[0][0]; t1 = red[0][1]; t2 = red[0][2];
+#pragma unroll
+        for (int w = 1; w < NW; ++w) { t0 += red[w][0]; t1 += red[w][1]; t2 += red[w][2]; }
+        if (lane == 0) pr->st->counter = 0u;
+        finish_pass(lp, pr, i, t0, t1, t2);
+      }
     }
     __syncthreads();
   }
