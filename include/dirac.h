@@ -117,8 +117,10 @@ dirac_status dirac_set_vector_potential(dirac_ctx* ctx, double A_x, double A_y);
  * |alpha_j + s| or beta_j so far).  psi_dev: device complex128 [ny][nx][2],
  * 32-byte aligned, owned by the caller.  If info is non-NULL the call
  * synchronises the stream and fills it; otherwise it returns after enqueueing.
- * Errors: DIRAC_EINVAL (m out of range, dt <= 0 or non-finite, tol < 0,
- * misaligned psi, dt too large for the small exponential: dt * ||H|| > 90),
+ * dt < 0 steps backwards in time, psi <- exp(+i H |dt|) psi (T is real, so
+ * the small exponential is the conjugate of the forward one).
+ * Errors: DIRAC_EINVAL (m out of range, dt = 0 or non-finite, tol < 0,
+ * misaligned psi, dt too large for the small exponential: |dt| ||H|| > 90),
  * DIRAC_ESTATE (no set_fields yet), DIRAC_ENONFINITE (only with info),
  * DIRAC_ECUDA.
  */
@@ -366,6 +368,70 @@ dirac_status dirac_lanczos_eigs(dirac_ctx* ctx, const void* start_dev, int n_wan
                                 int check_every, double tol, double e_lo, double e_hi, int reorth,
                                 int fold, double sigma, double* eigs_out, double* bounds_out,
                                 void* vecs_dev, dirac_eig_info* info);
+
+/* ------------------------------------------------------------------------
+ * Gradients through the propagation (adjoint of the time-discrete map)
+ * ------------------------------------------------------------------------ */
+
+enum { DIRAC_OBS_PX = 0, DIRAC_OBS_PROJ = 1 };
+
+typedef struct {
+    int observable;        /* DIRAC_OBS_PX: L = dx dy Re <psi_N, p_x psi_N>, p_x = -i D_x
+                              (the Hamiltonian's central difference);
+                              DIRAC_OBS_PROJ: L = |dx dy <phi, psi_N>|^2 */
+    const void* phi_dev;   /* PROJ: the fixed state phi (complex128 [ny][nx][2]) */
+    int checkpoint_every;  /* forward states kept every this many steps (>= 1) */
+    int block_x, block_y;  /* dV_dev receives dL/dV summed over blocks of
+                              block_x x block_y sites (1, 1: per site) */
+    int n_coef;            /* with W_host: A_x of step n = sum_k W[n][k] a_k */
+    const double* W_host;  /* nsteps x n_coef, row-major (host), or NULL */
+} dirac_adjoint_opts;
+
+typedef struct {
+    double ms_forward;     /* device time of the forward sweep and the observable */
+    double ms_backward;    /* of the backward sweep (recomputation included) */
+    int quadrature_nodes;  /* Gauss-Legendre nodes of the Frechet integral */
+    int checkpoints;       /* stored forward states */
+    long long launches;    /* kernels launched by the call (both contexts) */
+} dirac_adjoint_info;
+
+/*
+ * Gradient of a real observable of the final state psi_N of nsteps time
+ * steps psi_{n+1} = exp(-i H_n dt) psi_n (Sec. 4, Eq. 17, Krylov dimension
+ * m, the context's V and energy shift, H_n with the vector potential
+ * (A_xy_host[2n], A_xy_host[2n+1]) -- the step means of Eq. 16) with respect
+ * to the potential V at every site and to the step-mean vector potential of
+ * every step.  The paper has no counterpart; the map differentiated is the
+ * time-discrete propagation itself (its Krylov error, Eq. 18, is taken as
+ * negligible).
+ *
+ * Method: reverse (adjoint) sweep, lambda_N = dL/d conj(psi_N),
+ * lambda_n = exp(+i H_n dt) lambda_{n+1}; each step contributes
+ * dL/dtheta = 2 dt Im int_0^1 <exp(+i H_n dt s) lambda_{n+1}, dH_n/dtheta
+ * exp(-i H_n dt (1 - s)) psi_n> ds (the Frechet derivative of the
+ * exponential), evaluated exactly in the two Krylov spaces with a
+ * Gauss-Legendre rule in s.  Forward states are kept every checkpoint_every
+ * steps and recomputed segment by segment.
+ *
+ * psi0_dev: initial state (device, not modified).  loss_out: L (host).
+ * psiN_dev: NULL or receives psi_N.  dV_dev: NULL or a device array of
+ * (ny / block_y) x (nx / block_x) doubles receiving dL/dV summed over blocks
+ * (V is the potential energy).  dA_host: NULL or host nsteps x 2 doubles
+ * receiving dL/dA_x, dL/dA_y of every step.  da_host: NULL or host n_coef
+ * doubles receiving dL/da_k = sum_n W[n][k] dL/dA_x(n).  With all three
+ * NULL only the forward sweep and L are computed.  info may be NULL.
+ * The context must be FP64 with fields set; a second context with the same
+ * operator is created for the adjoint.  Device memory: about
+ * (nsteps / checkpoint_every + checkpoint_every + 3) fields plus one Krylov
+ * basis.  Synchronises.
+ * Errors: DIRAC_EINVAL (arguments, mixed-precision context, blocks that do not
+ * tile the grid, dt * ||H|| too large for the quadrature), DIRAC_ESTATE,
+ * DIRAC_ENOMEM, DIRAC_ENONFINITE, DIRAC_ECUDA.
+ */
+dirac_status dirac_adjoint_gradient(dirac_ctx* ctx, const void* psi0_dev, int nsteps, double dt, int m,
+                                    const double* A_xy_host, const dirac_adjoint_opts* opts,
+                                    double* loss_out, void* psiN_dev, void* dV_dev, double* dA_host,
+                                    double* da_host, dirac_adjoint_info* info);
 
 /*
  * Test hook for the device small-matrix exponential: v = exp(-i T dt) e_1 for

@@ -22,6 +22,7 @@ EIG_ITER_MAX = 8192
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ESTATE = range(6)
 PERIODIC, DIRICHLET = 0, 1
 FP64, MIXED = 0, 1
+OBS_PX, OBS_PROJ = 0, 1
 
 
 class StepInfoC(ctypes.Structure):
@@ -53,6 +54,19 @@ class EigInfoC(ctypes.Structure):
                 ("breakdown", ctypes.c_int), ("launches", ctypes.c_longlong),
                 ("ms_apply", ctypes.c_double), ("ms_dot", ctypes.c_double),
                 ("ms_update", ctypes.c_double), ("ms_other", ctypes.c_double)]
+
+
+class AdjointOptsC(ctypes.Structure):
+    _fields_ = [("observable", ctypes.c_int), ("phi_dev", ctypes.c_void_p),
+                ("checkpoint_every", ctypes.c_int), ("block_x", ctypes.c_int),
+                ("block_y", ctypes.c_int), ("n_coef", ctypes.c_int),
+                ("W_host", ctypes.POINTER(ctypes.c_double))]
+
+
+class AdjointInfoC(ctypes.Structure):
+    _fields_ = [("ms_forward", ctypes.c_double), ("ms_backward", ctypes.c_double),
+                ("quadrature_nodes", ctypes.c_int), ("checkpoints", ctypes.c_int),
+                ("launches", ctypes.c_longlong)]
 
 
 class DiracError(RuntimeError):
@@ -114,6 +128,8 @@ def lib():
         "dirac_apply_hamiltonian": (i, [vp, vp, vp]),
         "dirac_lanczos_eigs": (i, [vp, vp, i, i, i, d, d, d, i, i, d, dp, dp, vp,
                                    ctypes.POINTER(EigInfoC)]),
+        "dirac_adjoint_gradient": (i, [vp, vp, i, d, i, dp, ctypes.POINTER(AdjointOptsC), dp, vp, vp,
+                                       dp, dp, ctypes.POINTER(AdjointInfoC)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

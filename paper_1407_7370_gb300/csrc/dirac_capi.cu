@@ -487,7 +487,9 @@ dirac_status Engine::run(vec4* const* psi, int nsteps, double dt, int m, double 
     if (!psi[b] || !aligned32(psi[b])) return fail(DIRAC_EINVAL, "psi of problem %d null or not 32-byte aligned", b);
   }
   if (m < 1 || m > m_max) return fail(DIRAC_EINVAL, "m = %d outside 1..m_max = %d", m, m_max);
-  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(DIRAC_EINVAL, "dt must be finite and > 0");
+  if (!(dt != 0.0) || !std::isfinite(dt)) return fail(DIRAC_EINVAL, "dt must be finite and nonzero");
+  const bool backward = dt < 0.0;   // exp(+i H |dt|): the conjugate of the forward coefficients
+  dt = std::fabs(dt);
   if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(DIRAC_EINVAL, "tol must be finite and >= 0");
   if (nsteps < 0) return fail(DIRAC_EINVAL, "nsteps < 0");
   if (nsteps == 0) return DIRAC_OK;
@@ -589,6 +591,7 @@ dirac_status Engine::run(vec4* const* psi, int nsteps, double dt, int m, double 
   lp.m = m;
   lp.mcc = mcc;
   lp.dt = dt;
+  lp.conj_coef = backward ? 1 : 0;
   lp.tol = tol;
   lp.step = d_step;
   lp.redo_budget = redo_budget(precision, m);
@@ -746,7 +749,23 @@ dirac_status ctx_view(dirac_ctx* ctx, CtxView* v) {
   v->stream = e.stream;
   v->launches = &ctx->e.launches;
   v->profiling = e.profiling;
+  v->precision = e.precision;
+  v->m_max = e.m_max;
+  v->dev_state = e.d_st;
+  v->basis = q.basis;
   return DIRAC_OK;
+}
+
+dirac_status operator_interval(dirac_ctx* ctx, double ax_max, double ay_max, double* c0, double* half) {
+  if (!ctx) return fail(DIRAC_EINVAL, "null context");
+  const Engine& e = ctx->e;
+  const HostProblem& q = e.P[0];
+  spectral_interval(e.order, q.dx, q.dy, e.mass, e.c, ax_max, ay_max, q.vmin, q.vmax, q.shift, *c0, *half);
+  return DIRAC_OK;
+}
+
+dirac_status cheb_params(double c0, double half, double dt, double shift, ChebParams* cp) {
+  return make_cheb(c0, half, dt, shift, *cp);
 }
 
 }  // namespace dirac

@@ -25,8 +25,21 @@ struct CtxView {
   cudaStream_t stream;
   long long* launches;    // the context's kernel-launch counter
   bool profiling;         // dirac_profile_enable is on: time kernels with CUDA events
+  int precision;          // DIRAC_FP64 or DIRAC_MIXED
+  int m_max;
+  const void* dev_state;  // the problem's DevState (device): T, norms, k of the last step
+  void* basis;            // its Krylov basis q^_2 .. q^_{m_max} (device), consecutive fields
 };
 
 dirac_status ctx_view(dirac_ctx* ctx, CtxView* v);
+
+struct ChebParams;
+
+// [c0 - half, c0 + half] contains the spectrum of H - s for any vector
+// potential with |A_x| <= ax_max, |A_y| <= ay_max
+dirac_status operator_interval(dirac_ctx* ctx, double ax_max, double ay_max, double* c0, double* half);
+
+// Chebyshev coefficients of exp(-i (H - s) dt) e_1 on that interval (dt > 0)
+dirac_status cheb_params(double c0, double half, double dt, double shift, ChebParams* cp);
 
 }  // namespace dirac

@@ -138,7 +138,8 @@ struct LaunchParams {
   int nprob, total_tiles;
   int chunk_q, chunk_r;     // tiles per CTA: q + 1 for the first r CTAs, then q
   int pass, m, probe;
-  double mcc, dt, tol;
+  int conj_coef;            // 1: backward step (dt < 0): exp(+i H |dt|), the conjugate coefficients
+  double mcc, dt, tol;      // dt = |dt|
   const int* step;          // step counter of the running call (index into fields)
 };
 
@@ -184,8 +185,8 @@ __device__ __forceinline__ void cvt4(const From& a, To (&o)[4]) {
 // R = half * dt is sum_n eps_n (-i)^n J_n(R) T_n(X) (Jacobi-Anger), summed
 // with the three-term Chebyshev recurrence T_{n+1} = 2 X T_n - T_{n-1}.
 // ---------------------------------------------------------------------------
-__device__ void cheb_expm_e1(const ChebParams& cp, int k, double alpha_j, double beta_lo,
-                             double beta_hi, double& vr, double& vi) {
+__device__ inline void cheb_expm_e1(const ChebParams& cp, int k, double alpha_j, double beta_lo,
+                                    double beta_hi, double& vr, double& vi) {
   // lane j holds alpha_{j+1} and the couplings to its neighbours (0 outside)
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -221,8 +222,8 @@ __device__ void cheb_expm_e1(const ChebParams& cp, int k, double alpha_j, double
 // with plain loads up front; new values travel by shuffles.  rsqrt gives
 // sqrt(X), 1/X, sqrt(s2) and 1/sqrt(s2) with few dependent FP64 operations.
 // ---------------------------------------------------------------------------
-__device__ void finish_pass(const LaunchParams& lp, const Problem* pr, int i, double P, double Y,
-                            double X) {
+__device__ inline void finish_pass(const LaunchParams& lp, const Problem* pr, int i, double P, double Y,
+                                   double X) {
   DevState* st = pr->st;
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -326,7 +327,7 @@ __device__ void finish_pass(const LaunchParams& lp, const Problem* pr, int i, do
   if (lane < i) {
     const double f = nu1 * inv_nu_j;
     st->coef_re[lane + 1] = f * vr;
-    st->coef_im[lane + 1] = f * vi;
+    st->coef_im[lane + 1] = lp.conj_coef ? -f * vi : f * vi;   // T real: exp(+iT dt) e_1 = conj(exp(-iT dt) e_1)
   }
   if (lane == 0) {
     const double err = lp.dt * beta_hat * psi_norm * vk;
@@ -739,7 +740,7 @@ __global__ void __launch_bounds__(256) recombine(const __grid_constant__ RecombP
 // ---------------------------------------------------------------------------
 // test hook: exp(-i T dt) e_1 for a given T with the device routine
 // ---------------------------------------------------------------------------
-__global__ void debug_tridiag_expm(const __grid_constant__ ChebParams cp, int k, const double* alpha1,
+static __global__ void debug_tridiag_expm(const __grid_constant__ ChebParams cp, int k, const double* alpha1,
                                    const double* beta1, double* out_re, double* out_im) {
   double vr, vi;
   const int lane = threadIdx.x & 31;

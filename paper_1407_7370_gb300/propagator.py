@@ -42,6 +42,17 @@ class EigResult:
     ms: dict = None          # device ms per kernel kind while profiling (apply, dot, update, other)
 
 
+@dataclasses.dataclass
+class AdjointResult:
+    """Result of Propagator.adjoint_gradient."""
+    loss: float
+    dV: object = None        # CUDA float64 tensor (ny / by, nx / bx): dL/dV summed over blocks
+    dA: np.ndarray = None    # (nsteps, 2): dL/dA_x, dL/dA_y of every step
+    da: np.ndarray = None    # (n_coef,): dL/da_k for A_x = W a
+    psiN: object = None      # CUDA complex128 tensor (ny, nx, 2): the final state
+    info: dict = None
+
+
 def _torch():
     import torch
     return torch
@@ -175,6 +186,51 @@ class Propagator:
                          vec_t[:nf] if vec_t is not None else None, int(info.launches),
                          {"apply": info.ms_apply, "dot": info.ms_dot, "update": info.ms_update,
                           "other": info.ms_other})
+
+    def adjoint_gradient(self, psi0, nsteps: int, dt: float, m: int, A, observable: str = "px",
+                         phi=None, checkpoint_every: int = 50, block=(1, 1), W=None,
+                         grad_V: bool = True, grad_A: bool = True, return_state: bool = False
+                         ) -> AdjointResult:
+        """dirac_adjoint_gradient: L of psi_N and its gradients with respect to V
+        (summed over blocks (by, bx)) and the per-step vector potential A
+        ((nsteps, 2) array of step means); with W (nsteps x K), also dL/da for
+        A_x = W a."""
+        torch = _torch()
+        _check_psi(psi0, self.ny, self.nx)
+        self._sync_stream()
+        A = np.ascontiguousarray(A, dtype=np.float64).reshape(nsteps, 2)
+        opts = nat.AdjointOptsC()
+        opts.observable = {"px": nat.OBS_PX, "proj": nat.OBS_PROJ}[observable]
+        if phi is not None:
+            _check_psi(phi, self.ny, self.nx)
+            opts.phi_dev = phi.data_ptr()
+        opts.checkpoint_every = int(checkpoint_every)
+        by, bx = int(block[0]), int(block[1])
+        opts.block_x, opts.block_y = bx, by
+        W_arr = None
+        if W is not None:
+            W_arr = np.ascontiguousarray(W, dtype=np.float64).reshape(nsteps, -1)
+            opts.n_coef = W_arr.shape[1]
+            opts.W_host = W_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        loss = ctypes.c_double()
+        dV = torch.empty((self.ny // by, self.nx // bx), dtype=torch.float64,
+                         device=psi0.device) if grad_V else None
+        dA = np.zeros((nsteps, 2)) if grad_A else None
+        da = np.zeros(opts.n_coef) if (grad_A and W_arr is not None) else None
+        psiN = torch.empty_like(psi0) if return_state else None
+        info = nat.AdjointInfoC()
+        dptr = ctypes.POINTER(ctypes.c_double)
+        nat.check(nat.lib().dirac_adjoint_gradient(
+            self._ctx, ctypes.c_void_p(psi0.data_ptr()), nsteps, dt, m,
+            A.ctypes.data_as(dptr), ctypes.byref(opts), ctypes.byref(loss),
+            ctypes.c_void_p(psiN.data_ptr()) if psiN is not None else None,
+            ctypes.c_void_p(dV.data_ptr()) if dV is not None else None,
+            dA.ctypes.data_as(dptr) if dA is not None else None,
+            da.ctypes.data_as(dptr) if da is not None else None, ctypes.byref(info)))
+        return AdjointResult(loss.value, dV, dA, da, psiN,
+                             {"ms_forward": info.ms_forward, "ms_backward": info.ms_backward,
+                              "quadrature_nodes": info.quadrature_nodes,
+                              "checkpoints": info.checkpoints, "launches": int(info.launches)})
 
     def use_graphs(self, enable: bool = True):
         nat.check(nat.lib().dirac_use_graphs(self._ctx, 1 if enable else 0))
