@@ -68,6 +68,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
     ap.add_argument("--no-eigen", action="store_true", help="skip the eigenvalue-mode workload")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint workload")
     ap.add_argument("--only", choices=["fp64", "mixed"], default=None,
                     help="run one path only (for profiling); prints a partial line")
     return ap.parse_args()
@@ -391,6 +392,77 @@ def measure_eigen(torch, gi, pk):
     return out
 
 
+ADJ_CFG = dict(
+    name="adjoint: d<p_x>/dV (256x256 blocks of 4x4 sites) and d<p_x>/da (64 sine coefficients "
+         "of A_x), 1024x1024, dx=0.05, m=16, dt=2e-4, checkpoints every 50 steps, smoothed "
+         "Coulomb Z=1, a=0.5",
+    side=1024, dx=0.05, m=16, dt=2e-4, steps=400, full_steps=2000, ncoef=64, block=4, ckpt=50)
+CONTRACT_FLOPS_PER_SITE = 16 * 16 * 16   # 8 FMA per (j, l) pair of the two 16-vector bases
+
+
+def measure_adjoint(torch, gi, pk):
+    """The adjoint sweep of the 1024^2 gradient workload over `steps` steps (the
+    full run is `full_steps` steps at the same cost per step), then a short
+    profiled run for the contraction kernel's time."""
+    from paper_1407_7370_gb300 import Propagator
+    from paper_1407_7370_gb300.propagator import pulse_sine_basis_means
+    c = ADJ_CFG
+    C2 = 137.036 ** 2
+    g = wl.Grid(c["side"], c["side"], c["dx"], c["dx"])
+    V = wl.smoothed_coulomb(g, 1.0, 0.5)
+    b = c["block"]
+    Vb = V.reshape(g.ny // b, b, g.nx // b, b).mean(axis=(1, 3))
+    Vs = torch.from_numpy(np.repeat(np.repeat(Vb, b, 0), b, 1)).cuda().contiguous()
+    psi0 = torch.from_numpy(wl.positive_energy_packet(g, p0=(0.0, 0.0), sigma_x=0.7)).cuda()
+    prop = Propagator(g.nx, g.ny, g.dx, g.dy, m_max=c["m"])
+    prop.set_fields(Vs, shift=C2)
+
+    def run(nsteps, profile=False):
+        W = pulse_sine_basis_means(nsteps, c["dt"], c["ncoef"], nsteps * c["dt"])
+        coef = np.random.default_rng(5).uniform(-1.0, 1.0, c["ncoef"]) * 5.0 / (1.0 + np.arange(c["ncoef"]))
+        A = np.zeros((nsteps, 2))
+        A[:, 0] = W @ coef
+        prop.profile(profile)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream = torch.cuda.current_stream()
+        e0.record(stream)
+        r = prop.adjoint_gradient(psi0, nsteps, c["dt"], c["m"], A, observable="px",
+                                  checkpoint_every=c["ckpt"], block=(b, b), W=W)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prop.profile(False)
+        return r, e0.elapsed_time(e1) / 1e3
+
+    run(c["ckpt"])                                    # warm-up
+    clocks = ClockSampler(gi)
+    clocks.start()
+    res, t = run(c["steps"])
+    clk = clocks.stop()
+    prof, _ = run(c["ckpt"], profile=True)
+    n = g.n_sites
+    per_launch = prof.info["ms_contract"] / 1e3 / c["ckpt"]
+    flops = CONTRACT_FLOPS_PER_SITE * n / per_launch / 1e12
+    fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12
+    out = {"workload": c["name"], "steps": c["steps"], "full_config_steps": c["full_steps"],
+           "seconds": t, "ms_per_step": 1e3 * t / c["steps"],
+           "value": n * c["steps"] / t, "unit": "site-steps/s of the gradient (forward + adjoint)",
+           "full_config_seconds_estimate": t * c["full_steps"] / c["steps"],
+           "ms_forward": res.info["ms_forward"], "ms_backward": res.info["ms_backward"],
+           "quadrature_nodes": res.info["quadrature_nodes"], "gpu_launches": res.info["launches"],
+           "loss": res.loss, "clocks": clk,
+           "roofline": {"bound": "alu", "kernel": "adj_contract<16> (per-site bilinear form)",
+                        "achieved": flops, "peak": fp64_peak, "unit": "TFLOP/s",
+                        "frac": flops / fp64_peak, "traffic": None,
+                        "kernel_avg_us": per_launch * 1e6,
+                        "flops_per_site": CONTRACT_FLOPS_PER_SITE,
+                        "share_of_backward": prof.info["ms_contract"] / max(1e-9, prof.info["ms_backward"]),
+                        "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"}}
+    prop.close()
+    del Vs, psi0
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -503,6 +575,8 @@ def run_ours(args):
                 line["batched"]["mixed"]["value"] / line["value"]
         if not args.no_eigen:
             line["eigen"] = measure_eigen(torch, local, pk)
+        if not args.no_adjoint:
+            line["adjoint"] = measure_adjoint(torch, local, pk)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline()
         elif not args.no_cpu_baseline:

@@ -152,6 +152,13 @@ dirac_status dirac_sync(dirac_ctx* ctx);
  * [t0, t0 + dt], in closed form: the first Magnus term of Eq. 16. */
 double dirac_pulse_sin2_mean(double t0, double dt, double a0, double omega, double duration);
 
+/* Step means of the sine basis of a pulse, A_x(t) = sum_k a_k sin((k+1) pi t/T)
+ * on [0, T]: W[n * n_coef + k] = (1/dt) integral over [n dt, (n+1) dt] of
+ * sin((k+1) pi t/T) dt, in closed form (Eq. 16's first Magnus term for each
+ * basis function), so that the step means are W a.  W: host array of
+ * nsteps * n_coef doubles.  Errors: DIRAC_EINVAL. */
+dirac_status dirac_pulse_sine_basis_means(int nsteps, double dt, int n_coef, double duration, double* W);
+
 /* Number of kernels the library launched on this context so far. */
 long long dirac_kernel_launches(const dirac_ctx* ctx);
 
@@ -393,6 +400,8 @@ typedef struct {
     int quadrature_nodes;  /* Gauss-Legendre nodes of the Frechet integral */
     int checkpoints;       /* stored forward states */
     long long launches;    /* kernels launched by the call (both contexts) */
+    double ms_contract;    /* device time of the per-site contraction kernels, measured
+                              with CUDA events while dirac_profile_enable is on (else 0) */
 } dirac_adjoint_info;
 
 /*

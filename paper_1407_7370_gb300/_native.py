@@ -66,7 +66,7 @@ class AdjointOptsC(ctypes.Structure):
 class AdjointInfoC(ctypes.Structure):
     _fields_ = [("ms_forward", ctypes.c_double), ("ms_backward", ctypes.c_double),
                 ("quadrature_nodes", ctypes.c_int), ("checkpoints", ctypes.c_int),
-                ("launches", ctypes.c_longlong)]
+                ("launches", ctypes.c_longlong), ("ms_contract", ctypes.c_double)]
 
 
 class DiracError(RuntimeError):
@@ -103,6 +103,7 @@ def lib():
         "dirac_propagate_host": (i, [vp, vp, i, d, i, d, dp, ctypes.POINTER(StepInfoC)]),
         "dirac_sync": (i, [vp]),
         "dirac_pulse_sin2_mean": (d, [d, d, d, d, d]),
+        "dirac_pulse_sine_basis_means": (i, [i, d, i, d, dp]),
         "dirac_kernel_launches": (ctypes.c_longlong, [vp]),
         "dirac_status_string": (ctypes.c_char_p, [i]),
         "dirac_last_error": (ctypes.c_char_p, []),

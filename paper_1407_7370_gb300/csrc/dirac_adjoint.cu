@@ -549,6 +549,14 @@ dirac_status dirac_adjoint_gradient(dirac_ctx* ctx, const void* psi0_dev, int ns
   ca.qf = static_cast<const v4*>(v.basis);
   ca.pb = static_cast<const v4*>(vb_view.basis);
   ca.p1 = lam1; ca.M = Mm; ca.n = n; ca.gV = gV; ca.part = part;
+  // CUDA-event timing of the contraction kernels while the context profiles
+  cudaEvent_t cev[2];
+  for (auto& e : cev) ADJ_TRY(cudaEventCreate(&e));
+  struct CevGuard {
+    cudaEvent_t* e;
+    ~CevGuard() { for (int i = 0; i < 2; ++i) cudaEventDestroy(e[i]); }
+  } cevg{cev};
+  double ms_contract = 0.0;
   for (int c = n_ckpt - 1; c >= 0 && !zero_adjoint; --c) {
     const int n0 = c * K, cnt = std::min(K, nsteps - n0);
     // the segment's states psi_{n0} .. psi_{n0+cnt-1}
@@ -570,9 +578,17 @@ dirac_status dirac_adjoint_gradient(dirac_ctx* ctx, const void* psi0_dev, int ns
       adj_mmat<<<1, QMAX * 32, 0, s>>>(ma);
       ADJ_TRY(cudaGetLastError());
       ca.q1 = seg + (size_t)k * n;
+      if (v.profiling) ADJ_TRY(cudaEventRecord(cev[0], s));
       if (jw == 16) adj_contract<16><<<nblk, 256, 0, s>>>(ca);
       else adj_contract<32><<<nblk, 256, 0, s>>>(ca);
       ADJ_TRY(cudaGetLastError());
+      if (v.profiling) {   // profiling only: wait for this launch and add its time
+        float t = 0.f;
+        ADJ_TRY(cudaEventRecord(cev[1], s));
+        ADJ_TRY(cudaEventSynchronize(cev[1]));
+        ADJ_TRY(cudaEventElapsedTime(&t, cev[0], cev[1]));
+        ms_contract += t;
+      }
       adj_finish_a<<<1, 32, 0, s>>>(part, nblk, v.c, gA + 2 * step);   // dH/dA = c sigma (electron)
       ADJ_TRY(cudaGetLastError());
       launches += 3;
@@ -612,6 +628,7 @@ dirac_status dirac_adjoint_gradient(dirac_ctx* ctx, const void* psi0_dev, int ns
     info->quadrature_nodes = R;
     info->checkpoints = n_ckpt;
     info->launches = launches + steps_launches;
+    info->ms_contract = ms_contract;
   }
   return DIRAC_OK;
 }

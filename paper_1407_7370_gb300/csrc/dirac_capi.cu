@@ -880,6 +880,21 @@ double dirac_pulse_sin2_mean(double t0, double dt, double a0, double omega, doub
   return a0 * (0.5 * integ(omega) - 0.25 * integ(omega + W) - 0.25 * integ(omega - W)) / dt;
 }
 
+dirac_status dirac_pulse_sine_basis_means(int nsteps, double dt, int n_coef, double duration, double* W) {
+  if (nsteps < 1 || n_coef < 1 || !W) return fail(DIRAC_EINVAL, "bad sizes or null output");
+  if (!(dt > 0.0) || !(duration > 0.0) || !std::isfinite(dt) || !std::isfinite(duration))
+    return fail(DIRAC_EINVAL, "dt and duration must be finite and > 0");
+  for (int n = 0; n < nsteps; ++n) {
+    const double a = n * dt, b = a + dt;
+    for (int k = 0; k < n_coef; ++k) {
+      const double w = (k + 1) * M_PI / duration;
+      // (cos(w a) - cos(w b)) / (w dt), written without cancellation
+      W[(size_t)n * n_coef + k] = 2.0 * std::sin(0.5 * w * (a + b)) * std::sin(0.5 * w * dt) / (w * dt);
+    }
+  }
+  return DIRAC_OK;
+}
+
 long long dirac_kernel_launches(const dirac_ctx* ctx) { return ctx ? ctx->e.launches : 0; }
 
 dirac_status dirac_profile_enable(dirac_ctx* ctx, int enable) {

@@ -230,7 +230,8 @@ class Propagator:
         return AdjointResult(loss.value, dV, dA, da, psiN,
                              {"ms_forward": info.ms_forward, "ms_backward": info.ms_backward,
                               "quadrature_nodes": info.quadrature_nodes,
-                              "checkpoints": info.checkpoints, "launches": int(info.launches)})
+                              "checkpoints": info.checkpoints, "launches": int(info.launches),
+                              "ms_contract": info.ms_contract})
 
     def use_graphs(self, enable: bool = True):
         nat.check(nat.lib().dirac_use_graphs(self._ctx, 1 if enable else 0))
@@ -273,6 +274,14 @@ def pulse_schedule(t0: float, dt: float, nsteps: int, a0: float, omega: float, d
     for n in range(nsteps):
         out[n, 0] = pulse_sin2_mean(t0 + n * dt, dt, a0, omega, duration)
     return out
+
+
+def pulse_sine_basis_means(nsteps: int, dt: float, n_coef: int, duration: float) -> np.ndarray:
+    """(nsteps, n_coef) step means of sin((k+1) pi t / T) (library, closed form)."""
+    W = np.zeros((nsteps, n_coef))
+    nat.check(nat.lib().dirac_pulse_sine_basis_means(
+        nsteps, dt, n_coef, duration, W.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return W
 
 
 def tridiag_expm_device(alpha, beta, dt: float, lo: float, hi: float) -> np.ndarray:

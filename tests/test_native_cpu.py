@@ -37,6 +37,15 @@ def test_pulse_mean_matches_oracle_quadrature(lib):
         assert abs(a - b) <= 1e-13 * p.a0
 
 
+def test_sine_basis_means_match_oracle(lib):
+    import numpy as np
+    from oracle import adjoint as adj
+    from paper_1407_7370_gb300.propagator import pulse_sine_basis_means
+    for nsteps, dt, k, T in ((7, 0.01, 5, 0.37), (2000, 2e-4, 64, 0.4)):
+        W = pulse_sine_basis_means(nsteps, dt, k, T)
+        assert np.max(np.abs(W - adj.sine_basis_means(nsteps, dt, k, T))) <= 1e-12
+
+
 def test_create_rejects_bad_arguments_before_touching_the_gpu(lib):
     ctx = ctypes.c_void_p()
     bad = [
