@@ -170,6 +170,18 @@ __device__ __forceinline__ int wrap(int g, int n, bool& outside) {
   return r < 0 ? r + n : r;
 }
 
+// read-only (non-coherent) loads: the inputs of a pass are not written
+// during it, and the compiler may then move these loads ahead of the shared
+// memory stores in between
+__device__ __forceinline__ vec4 ldg4(const vec4* p) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+  const double2 a = __ldg(q), b = __ldg(q + 1);
+  vec4 r;
+  r.x = a.x; r.y = a.y; r.z = b.x; r.w = b.y;
+  return r;
+}
+__device__ __forceinline__ float4 ldg4(const float4* p) { return __ldg(p); }
+
 template <class S> struct Vec4;
 template <> struct Vec4<double> { using T = double4_32a; };
 template <> struct Vec4<float> { using T = float4; };
@@ -475,16 +487,16 @@ lanczos_pass(const __grid_constant__ LaunchParams lp) {
         const size_t idx = (size_t)iy * nx + ix;
         if (q64) {
           const vec4* qsrc = (i == 1) ? pr->psi : static_cast<const vec4*>(q_prev);
-          cvt4(qsrc[idx], qp);
+          cvt4(ldg4(qsrc + idx), qp);
         } else {
-          cvt4(static_cast<const float4*>(q_prev)[idx], qp);
+          cvt4(ldg4(static_cast<const float4*>(q_prev) + idx), qp);
         }
         if (i == 1) {
 #pragma unroll
           for (int c = 0; c < 4; ++c) q[c] = qp[c];
         } else {
           S yv[4];
-          cvt4(yprev[idx], yv);
+          cvt4(ldg4(yprev + idx), yv);
 #pragma unroll
           for (int c = 0; c < 4; ++c) q[c] = fma(-gdS, qp[c], gS * yv[c]);
         }
