@@ -69,7 +69,11 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
     ap.add_argument("--no-eigen", action="store_true", help="skip the eigenvalue-mode workload")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint workload")
-    ap.add_argument("--only", choices=["fp64", "mixed"], default=None,
+    ap.add_argument("--eigen-side", type=int, default=None,
+                    help="grid side of the eigen workload (default: the configured 2048)")
+    ap.add_argument("--eigen-iters", type=int, default=None, help="Lanczos iterations of the eigen workload")
+    ap.add_argument("--adjoint-steps", type=int, default=None, help="steps of the adjoint workload")
+    ap.add_argument("--only", choices=["fp64", "mixed", "eigen", "adjoint"], default=None,
                     help="run one path only (for profiling); prints a partial line")
     return ap.parse_args()
 
@@ -337,11 +341,16 @@ GS_FLOPS_PER_SITE_VECTOR = 64   # two Gram-Schmidt passes x (inner product 16 + 
 GS_BYTES_PER_SITE_VECTOR = 128  # two passes x (read q_j for the products + read q_j for the update)
 
 
-def measure_eigen(torch, gi, pk):
+def measure_eigen(torch, gi, pk, side=None, iters=None):
     """Eigenvalue mode on the 2048^2 smoothed-Coulomb workload: one untimed
-    short call, then one timed call with per-kernel CUDA-event timing."""
+    short call, then one timed call with per-kernel CUDA-event timing (side
+    and iters override the grid and the iteration count, for profiling)."""
     from paper_1407_7370_gb300 import Propagator
-    c = EIGEN_CFG
+    c = dict(EIGEN_CFG)
+    if side:
+        c["side"] = side
+    if iters:
+        c["max_iter"] = iters
     C2 = 137.036 ** 2
     g = wl.Grid(c["side"], c["side"], c["dx"], c["dx"])
     V = torch.from_numpy(wl.smoothed_coulomb(g, c["z"], c["a"])).cuda()
@@ -405,13 +414,15 @@ ADJ_CFG = dict(
 CONTRACT_FLOPS_PER_SITE = 16 * 16 * 16   # 8 FMA per (j, l) pair of the two 16-vector bases
 
 
-def measure_adjoint(torch, gi, pk):
+def measure_adjoint(torch, gi, pk, steps=None):
     """The adjoint sweep of the 1024^2 gradient workload over `steps` steps (the
     full run is `full_steps` steps at the same cost per step), then a short
     profiled run for the contraction kernel's time."""
     from paper_1407_7370_gb300 import Propagator
     from paper_1407_7370_gb300.propagator import pulse_sine_basis_means
-    c = ADJ_CFG
+    c = dict(ADJ_CFG)
+    if steps:
+        c["steps"] = steps
     C2 = 137.036 ** 2
     g = wl.Grid(c["side"], c["side"], c["dx"], c["dx"])
     V = wl.smoothed_coulomb(g, 1.0, 0.5)
@@ -490,6 +501,14 @@ def run_ours(args):
     pk = peaks()
     hbm_peak = pk.get("hbm_gbs", 6800.0)
     hbm_src = "MEASURED_PEAKS.json hbm_gbs (burst copy)" if "hbm_gbs" in pk else "fallback 6.8 TB/s"
+    if args.only in ("eigen", "adjoint"):   # one workload alone (profiling runs)
+        if args.only == "eigen":
+            r = measure_eigen(torch, local, pk, args.eigen_side, args.eigen_iters)
+        else:
+            r = measure_adjoint(torch, local, pk, args.adjoint_steps)
+        if rank == 0:
+            print(json.dumps({"partial": args.only, "result": r}), flush=True)
+        return 0
     runs = {}
     for prec in ((args.only,) if args.only else ("fp64", "mixed")):
         prop = Propagator(g.nx, g.ny, g.dx, g.dy, m_max=m, precision=prec)
@@ -579,9 +598,9 @@ def run_ours(args):
             line["batched"]["speedup_mixed_batched_vs_fp64_single"] = \
                 line["batched"]["mixed"]["value"] / line["value"]
         if not args.no_eigen:
-            line["eigen"] = measure_eigen(torch, local, pk)
+            line["eigen"] = measure_eigen(torch, local, pk, args.eigen_side, args.eigen_iters)
         if not args.no_adjoint:
-            line["adjoint"] = measure_adjoint(torch, local, pk)
+            line["adjoint"] = measure_adjoint(torch, local, pk, args.adjoint_steps)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline()
         elif not args.no_cpu_baseline:
