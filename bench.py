@@ -43,7 +43,7 @@ PASS_FLOPS_PER_SITE = 80   # FP64 flops of one Lanczos iteration per site (see D
 
 # DRAM traffic per launch from the last ncu capture of the pass kernel, valid
 # only for the kernel source it was taken with (sha1 of dirac_kernels.cuh).
-TRAFFIC = {"fp64": ("a5693c562fe9", 69.62e6 + 20.36e6), "mixed": ("a5693c562fe9", 33.62e6 + 0.62e6)}
+TRAFFIC = {"fp64": ("3152f37e21a3", 69.54e6 + 19.63e6), "mixed": ("3152f37e21a3", 33.63e6 + 0.50e6)}
 
 
 def kernel_sha() -> str:
