@@ -83,6 +83,22 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", "1")))
 
 
+def max_over_ranks(t: float, world: int, dist, device) -> float:
+    """The slowest rank's time (every rank gets it)."""
+    if world > 1:
+        import torch
+        tt = torch.tensor([t], device=device, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return t
+
+
+def job_rate(units_per_rank: float, t_local: float, world: int, dist, device) -> float:
+    """Whole-job throughput of independent replicas: the units of all ranks over
+    the slowest rank's time."""
+    return world * units_per_rank / max_over_ranks(t_local, world, dist, device)
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -209,12 +225,8 @@ def measure(prop, psi, A, K, W, world, dist, torch, gi):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(t):
-        if world > 1:
-            tt = torch.tensor([t], device="cuda", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = float(tt.item())
-        return t
+    def slowest(t):
+        return max_over_ranks(t, world, dist, "cuda")
 
     prop.steps(psi, W, dt, m, A=A[:W])
     barrier()
@@ -229,7 +241,7 @@ def measure(prop, psi, A, K, W, world, dist, torch, gi):
     barrier()
     launches = prop.kernel_launches - l0
     clk = clocks.stop()
-    t = max_over_ranks(e0.elapsed_time(e1) / 1e3)
+    t = slowest(e0.elapsed_time(e1) / 1e3)
     result = psi.clone()
     prop.profile(True)
     info = prop.steps(psi, K, dt, m, A=A[W + K:W + 2 * K], info=True)
@@ -241,7 +253,7 @@ def measure(prop, psi, A, K, W, world, dist, torch, gi):
     w0 = time.perf_counter()
     for n in range(Ke):
         prop.propagate_host(host, 1, dt, m, A=A[W + (n % K):W + (n % K) + 1])
-    te = max_over_ranks(time.perf_counter() - w0)
+    te = slowest(time.perf_counter() - w0)
     return dict(t=t, launches=launches, clocks=clk, result=result, info=info, prof=prof,
                 te=te, Ke=Ke)
 
