@@ -353,7 +353,10 @@ typedef struct {
  *     min(sqrt(r), r / sqrt(theta)) from the Eq. 9 bound r; returned
  *     ascending in lambda.  e_lo, e_hi are not used.
  * At a breakdown (invariant subspace) the recurrence stops and T_k's spectrum
- * is exact.  At most DIRAC_EIG_RITZ_MAX Ritz values (the lowest in the window)
+ * is exact.  On a DIRAC_MIXED context the stencil products run in FP32 (the
+ * vectors rounded to complex64, the diagonal as a float plus its remainder);
+ * the Lanczos combination, the Gram-Schmidt passes, T and the Ritz values and
+ * vectors stay FP64.  At most DIRAC_EIG_RITZ_MAX Ritz values (the lowest in the window)
  * are examined per check.
  *
  * eigs_out, bounds_out: host arrays of n_want doubles; the first

@@ -108,9 +108,9 @@ struct ApplyArgs {
   int prologue;         // 1: s_i and beta_{i-1} from norm_part, breakdown test, scale by s_i
 };
 
-template <bool DIRI>
+template <bool DIRI, class T>
 __device__ __forceinline__ void load_site(const v4* __restrict__ in, int gx, int gy, int nx, int ny,
-                                          double (&o)[4]) {
+                                          T (&o)[4]) {
   if (DIRI) {
     if (gx < 0 || gx >= nx || gy < 0 || gy >= ny) { o[0] = o[1] = o[2] = o[3] = 0.0; return; }
   } else {
@@ -118,10 +118,13 @@ __device__ __forceinline__ void load_site(const v4* __restrict__ in, int gx, int
     gy = ((gy % ny) + ny) % ny;
   }
   const v4 v = in[(size_t)gy * nx + gx];
-  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  o[0] = (T)v.x; o[1] = (T)v.y; o[2] = (T)v.z; o[3] = (T)v.w;
 }
 
-template <int R, bool DIRI, bool HAS_V>
+// T = double: the FP64 product.  T = float: the mixed-precision product --
+// the stencil on FP32 copies of the vector (the diagonal as a float plus its
+// remainder), the Lanczos combination s_i y - c q^_{i-1} in FP64.
+template <int R, bool DIRI, bool HAS_V, class T>
 __global__ void __launch_bounds__(256) eig_apply(const ApplyArgs a) {
   __shared__ double sh_nrm;
   __shared__ int sh_stop;
@@ -164,7 +167,7 @@ __global__ void __launch_bounds__(256) eig_apply(const ApplyArgs a) {
   const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
   if (x >= a.nx || y >= a.ny) return;
   const int nx = a.nx, ny = a.ny;
-  double C[4], xp[4], xm[4], yp[4], ym[4], dxv[4], dyv[4];
+  T C[4], xp[4], xm[4], yp[4], ym[4], dxv[4], dyv[4];
   load_site<DIRI>(a.in, x, y, nx, ny, C);
   load_site<DIRI>(a.in, x + 1, y, nx, ny, xp);
   load_site<DIRI>(a.in, x - 1, y, nx, ny, xm);
@@ -179,25 +182,34 @@ __global__ void __launch_bounds__(256) eig_apply(const ApplyArgs a) {
     load_site<DIRI>(a.in, x, y - 2, nx, ny, ym);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      dxv[q] = fma(8.0, dxv[q], xm[q] - xp[q]);
-      dyv[q] = fma(8.0, dyv[q], ym[q] - yp[q]);
+      dxv[q] = fma(T(8), dxv[q], xm[q] - xp[q]);
+      dyv[q] = fma(T(8), dyv[q], ym[q] - yp[q]);
     }
   }
   const size_t idx = (size_t)y * nx + x;
-  double au = a.au, ad = a.ad;
+  const T au_hi = (T)a.au, ad_hi = (T)a.ad;
+  const T au_lo = (T)(a.au - (double)au_hi), ad_lo = (T)(a.ad - (double)ad_hi);
+  T au = au_hi, ad = ad_hi;
   if (HAS_V) {
-    const double v = a.V[idx];
+    const T v = (T)a.V[idx];
     au += v;
     ad += v;
   }
-  const double kx = a.kx, ky = a.ky, cax = a.cax, cay = a.cay;
-  double o[4];
+  const T kx = (T)a.kx, ky = (T)a.ky, cax = (T)a.cax, cay = (T)a.cay;
+  T ot[4];
   // upper: (mc^2+V-e0) u + c[-i D_x d - D_y d + (A_x - i A_y) d]
-  o[0] = au * C[0] + kx * dxv[3] - ky * dyv[2] + cax * C[2] + cay * C[3];
-  o[1] = au * C[1] - kx * dxv[2] - ky * dyv[3] + cax * C[3] - cay * C[2];
+  ot[0] = au * C[0] + kx * dxv[3] - ky * dyv[2] + cax * C[2] + cay * C[3];
+  ot[1] = au * C[1] - kx * dxv[2] - ky * dyv[3] + cax * C[3] - cay * C[2];
   // lower: (-mc^2+V-e0) d + c[-i D_x u + D_y u + (A_x + i A_y) u]
-  o[2] = ad * C[2] + kx * dxv[1] + ky * dyv[0] + cax * C[0] - cay * C[1];
-  o[3] = ad * C[3] - kx * dxv[0] + ky * dyv[1] + cax * C[1] + cay * C[0];
+  ot[2] = ad * C[2] + kx * dxv[1] + ky * dyv[0] + cax * C[0] - cay * C[1];
+  ot[3] = ad * C[3] - kx * dxv[0] + ky * dyv[1] + cax * C[1] + cay * C[0];
+  if constexpr (sizeof(T) == sizeof(float)) {
+    ot[0] = fma(au_lo, C[0], ot[0]);
+    ot[1] = fma(au_lo, C[1], ot[1]);
+    ot[2] = fma(ad_lo, C[2], ot[2]);
+    ot[3] = fma(ad_lo, C[3], ot[3]);
+  }
+  const double o[4] = {(double)ot[0], (double)ot[1], (double)ot[2], (double)ot[3]};
   v4 r;
   if (csub != 0.0) {
     const v4 sv = a.sub[idx];
@@ -758,19 +770,25 @@ ApplyArgs apply_args(const CtxView& v, double e0) {
   return a;
 }
 
-template <int R, bool D>
+template <int R, bool D, class T>
 cudaError_t launch_apply_rd(const ApplyArgs& a, cudaStream_t s) {
   const dim3 grid((a.nx + 31) / 32, (a.ny + 7) / 8);
-  if (a.V) eig_apply<R, D, true><<<grid, 256, 0, s>>>(a);
-  else eig_apply<R, D, false><<<grid, 256, 0, s>>>(a);
+  if (a.V) eig_apply<R, D, true, T><<<grid, 256, 0, s>>>(a);
+  else eig_apply<R, D, false, T><<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_apply(const CtxView& v, const ApplyArgs& a) {
-  if (v.order == 2) return v.boundary == DIRAC_DIRICHLET ? launch_apply_rd<1, true>(a, v.stream)
-                                                         : launch_apply_rd<1, false>(a, v.stream);
-  return v.boundary == DIRAC_DIRICHLET ? launch_apply_rd<2, true>(a, v.stream)
-                                       : launch_apply_rd<2, false>(a, v.stream);
+template <class T>
+cudaError_t launch_apply_t(const CtxView& v, const ApplyArgs& a) {
+  if (v.order == 2) return v.boundary == DIRAC_DIRICHLET ? launch_apply_rd<1, true, T>(a, v.stream)
+                                                         : launch_apply_rd<1, false, T>(a, v.stream);
+  return v.boundary == DIRAC_DIRICHLET ? launch_apply_rd<2, true, T>(a, v.stream)
+                                       : launch_apply_rd<2, false, T>(a, v.stream);
+}
+
+// f32: the mixed-precision product (the Lanczos steps of a DIRAC_MIXED context)
+cudaError_t launch_apply(const CtxView& v, const ApplyArgs& a, bool f32 = false) {
+  return f32 ? launch_apply_t<float>(v, a) : launch_apply_t<double>(v, a);
 }
 
 // Device time per kernel kind from CUDA events recorded between consecutive
@@ -990,21 +1008,22 @@ dirac_status dirac_lanczos_eigs(dirac_ctx* ctx, const void* start_dev, int n_wan
     a.ed = ed; a.norm_part = npart; a.n_part = n_upd; a.beta = beta; a.s = sarr; a.iter = i;
     a.prologue = 1;
     a.in = qi;
+    const bool f32 = v.precision == DIRAC_MIXED;
     if (!fold) {
       a.sub = qim;
       a.out = z;
-      EIG_TRY(launch_apply(v, a));
+      EIG_TRY(launch_apply(v, a, f32));
       EIG_TRY(tm.mark(K_APPLY));
     } else {
       a.sub = nullptr;
       a.out = tmp;
-      EIG_TRY(launch_apply(v, a));
+      EIG_TRY(launch_apply(v, a, f32));
       EIG_TRY(tm.mark(K_APPLY));
       a.prologue = 0;
       a.in = tmp;
       a.sub = qim;
       a.out = z;
-      EIG_TRY(launch_apply(v, a));
+      EIG_TRY(launch_apply(v, a, f32));
       EIG_TRY(tm.mark(K_APPLY));
     }
     const int passes = reorth ? 2 : 1;

@@ -31,9 +31,10 @@ def built():
         pytest.fail("GPU tests need a CUDA device")
 
 
-def make(grid, V=None, A=(0.0, 0.0), shift=0.0, order=2, boundary="periodic"):
+def make(grid, V=None, A=(0.0, 0.0), shift=0.0, order=2, boundary="periodic", precision="fp64"):
     from paper_1407_7370_gb300 import Propagator
-    p = Propagator(grid.nx, grid.ny, grid.dx, grid.dy, order=order, boundary=boundary, m_max=4)
+    p = Propagator(grid.nx, grid.ny, grid.dx, grid.dy, order=order, boundary=boundary, m_max=4,
+                   precision=precision)
     p.set_fields(None if V is None else torch.from_numpy(np.ascontiguousarray(V)).cuda(), A=A,
                  shift=shift)
     op = ham.Operator(grid.nx, grid.ny, grid.dx, grid.dy, order=order,
@@ -259,3 +260,20 @@ def test_eigs_launch_count_and_kernel_timing():
     # start vector + 30 x (product + 2 x (inner products, sums, update)) + 3 checks x 3
     assert res.launches == 1 + 30 * 7 + 3 * 3
     assert res.ms["apply"] > 0 and res.ms["dot"] > 0 and res.ms["update"] > 0 and res.ms["other"] > 0
+
+
+def test_eigs_mixed_stencil_close_to_fp64():
+    """FP32 stencil products with FP64 reorthogonalisation and Ritz values:
+    the eigenvalues move by about u32 times the size of (H - s) on the
+    states (their lower components carry the -2 m c^2 diagonal)."""
+    g, V, start = soft_core_case(24, 20, 0.3, 2.0)
+    window = (-C * C, 0.0)
+    p64, op = make(g, V=V, shift=C * C)
+    p32, _ = make(g, V=V, shift=C * C, precision="mixed")
+    r64 = p64.eigs(dev(start), n_want=64, max_iter=150, tol=1e-9, window=window)
+    r32 = p32.eigs(dev(start), n_want=64, max_iter=150, tol=1e-6, window=window)
+    assert r32.values.size >= 2
+    ref = lz.lanczos_eigs(op, start, n_want=64, max_iter=150, tol=1e-9, window=window)
+    for v in r32.values:
+        assert np.min(np.abs(ref.values - v)) <= 1e-5 * max(1.0, abs(v))
+    assert np.max(np.abs(r64.values - ref.values[: r64.values.size])) <= 1e-11 * norm_a(op)
