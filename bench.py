@@ -43,7 +43,7 @@ PASS_FLOPS_PER_SITE = 80   # FP64 flops of one Lanczos iteration per site (see D
 
 # DRAM traffic per launch from the last ncu capture of the pass kernel, valid
 # only for the kernel source it was taken with (sha1 of dirac_kernels.cuh).
-TRAFFIC = {"fp64": ("3152f37e21a3", 69.54e6 + 19.63e6), "mixed": ("3152f37e21a3", 33.63e6 + 0.50e6)}
+TRAFFIC = {"fp64": ("69d9e39dafda", 69.59e6 + 20.07e6), "mixed": ("69d9e39dafda", 33.63e6 + 0.65e6)}
 
 
 def kernel_sha() -> str:
@@ -395,7 +395,9 @@ def measure_eigen(torch, gi, pk, side=None, iters=None):
     pm.set_fields(V, shift=C2)
     em0, em1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     em0.record(stream)
-    resm = pm.eigs(st, n_want=c["n_want"], max_iter=c["max_iter"], tol=max(c["tol"], 1e-6),
+    # FP32 products limit the residual to about u32 c sqrt(2) / dx (6e-4 au
+    # here, 2e-5 of the lowest |lambda|): ask for no more than that
+    resm = pm.eigs(st, n_want=c["n_want"], max_iter=c["max_iter"], tol=max(c["tol"], 2e-5),
                    window=window, check_every=c["check_every"])
     em1.record(stream)
     torch.cuda.synchronize()
@@ -404,7 +406,8 @@ def measure_eigen(torch, gi, pk, side=None, iters=None):
     mixed = {"seconds": em0.elapsed_time(em1) / 1e3, "iterations": resm.iterations,
              "values_minus_mc2": [float(v) for v in resm.values],
              "max_abs_diff_vs_fp64": max(diffs) if diffs else None,
-             "note": "FP32 stencil products, FP64 Gram-Schmidt, T and Ritz values"}
+             "tol": max(c["tol"], 2e-5),
+             "note": "FP32 off-diagonal stencil products, FP64 diagonal, Gram-Schmidt, T and Ritz values"}
     k, n = res.iterations, g.n_sites
     gs_ms = res.ms["dot"] + res.ms["update"]
     flops = GS_FLOPS_PER_SITE_VECTOR * n * k * (k + 1) / 2

@@ -204,10 +204,11 @@ dirac_status dirac_batch_set_fields(dirac_batch* batch, int problem, const doubl
                                     double A_x, double A_y, double energy_shift);
 
 /*
- * Launch shape of the Lanczos passes: tile height 32 or 16 sites (mixed
- * precision only; FP64 always uses 32) and a cap on resident CTAs per SM
- * (0: no cap).  Used by the autotuner; results do not depend on it beyond
- * the order of floating-point sums.
+ * Launch shape of the Lanczos passes: tile height 32 or 16 sites and a cap
+ * on resident CTAs per SM (0: no cap).  Without a call the tile height is
+ * chosen per run (FP64: from the tile count per SM; mixed: 16).  Used by the
+ * autotuner; results do not depend on it beyond the order of floating-point
+ * sums.
  */
 dirac_status dirac_batch_set_launch_shape(dirac_batch* batch, int tile_height, int ctas_per_sm);
 
@@ -353,9 +354,10 @@ typedef struct {
  *     min(sqrt(r), r / sqrt(theta)) from the Eq. 9 bound r; returned
  *     ascending in lambda.  e_lo, e_hi are not used.
  * At a breakdown (invariant subspace) the recurrence stops and T_k's spectrum
- * is exact.  On a DIRAC_MIXED context the stencil products run in FP32 (the
- * vectors rounded to complex64, the diagonal as a float plus its remainder);
- * the Lanczos combination, the Gram-Schmidt passes, T and the Ritz values and
+ * is exact.  On a DIRAC_MIXED context the off-diagonal part of the stencil
+ * products (differences, vector potential) runs in FP32 on complex64 copies
+ * of the vectors and the diagonal (+-m c^2 + V - s) in FP64; the Lanczos
+ * combination, the Gram-Schmidt passes, T and the Ritz values and
  * vectors stay FP64.  At most DIRAC_EIG_RITZ_MAX Ritz values (the lowest in the window)
  * are examined per check.
  *

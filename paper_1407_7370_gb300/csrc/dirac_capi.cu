@@ -158,10 +158,15 @@ struct LaunchShape {
 // Persistent launch: as many CTAs as are resident at once (at most one per
 // tile), each taking a contiguous chunk of the tile list whose size differs
 // from the others' by at most one tile.
+#ifndef DIRAC_ASYNC_MIN_TILES
+#define DIRAC_ASYNC_MIN_TILES 4
+#endif
+constexpr int ASYNC_MIN_TILES = DIRAC_ASYNC_MIN_TILES;
+
 template <class S, int R, int TH, bool D, bool V>
 cudaError_t launch_pass_t(LaunchParams p, const LaunchShape& ls, cudaStream_t s) {
   static int occ = 0;
-  constexpr int NT = sub_workers<S>() * 32 * (TH / RPT);
+  constexpr int NT = sub_workers<S>() * 32 * (TH / rows_per_thread<S, TH>());
   constexpr size_t smem = dyn_smem_bytes<S, R, TH, sub_workers<S>()>();
   if (occ == 0) {
     cudaError_t e = cudaSuccess;
@@ -179,6 +184,9 @@ cudaError_t launch_pass_t(LaunchParams p, const LaunchShape& ls, cudaStream_t s)
   const int grid = std::max(1, std::min(p.total_tiles, slots));
   p.chunk_q = p.total_tiles / grid;
   p.chunk_r = p.total_tiles % grid;
+  // asynchronous tile staging pays once each CTA has several tiles to stream
+  // (a grid much larger than L2 holds); below that the extra barrier costs more
+  p.async_tiles = p.chunk_q >= ASYNC_MIN_TILES;
   return launch_pdl(lanczos_pass<S, R, TH, D, V>, grid, NT, smem, s, p);
 }
 
@@ -197,7 +205,10 @@ cudaError_t launch_pass_s(int order, bool diri, bool hasv, const LaunchParams& p
 // and 2 read the complex128 state as q^_1; the kernel picks per problem).
 cudaError_t launch_pass(int precision, int order, bool diri, bool hasv, const LaunchParams& p,
                         const LaunchShape& ls, cudaStream_t s) {
-  if (precision == DIRAC_FP64) return launch_pass_s<double, 32>(order, diri, hasv, p, ls, s);
+  if (precision == DIRAC_FP64) {
+    if (ls.th == 16) return launch_pass_s<double, 16>(order, diri, hasv, p, ls, s);
+    return launch_pass_s<double, 32>(order, diri, hasv, p, ls, s);
+  }
   if (ls.th == 16) return launch_pass_s<float, 16>(order, diri, hasv, p, ls, s);
   return launch_pass_s<float, 32>(order, diri, hasv, p, ls, s);
 }
@@ -345,6 +356,24 @@ dirac_status check_grid(int nx, int ny, double dx, double dy) {
 // tiles of a problem at tile height th
 int tiles_of(int nx, int ny, int th) { return ((nx + TILE_W - 1) / TILE_W) * ((ny + th - 1) / th); }
 
+// FP64 tile height when none is set.  One CTA per SM streams its chunk of
+// tiles, so the SM with the most tiles sets the pass time:
+// ceil(tiles / SMs) x (rows + about a quarter row of per-tile cost: halo,
+// barriers).  16-row tiles win on grids that leave SMs idle or end with a
+// nearly empty last tile per SM; 32-row tiles otherwise.
+int fp64_tile_height(const std::vector<HostProblem>& P, int n_sm) {
+  double best = 1e300;
+  int pick = 32;
+  for (int th : {32, 16}) {
+    long long t = 0;
+    for (const HostProblem& q : P) t += tiles_of(q.nx, q.ny, th);
+    const long long per_sm = (t + n_sm - 1) / std::max(1, n_sm);
+    const double cost = (double)per_sm * (th + 0.25);
+    if (cost < best) { best = cost; pick = th; }
+  }
+  return pick;
+}
+
 dirac_status Engine::init(int n, const int* nx, const int* ny, const double* dx, const double* dy,
                           double mass_, double c_, int order_, int boundary_, int precision_, int m_max_,
                           void* stream_) {
@@ -353,7 +382,7 @@ dirac_status Engine::init(int n, const int* nx, const int* ny, const double* dx,
   int dev = 0;
   CUDA_TRY(cudaGetDevice(&dev));
   CUDA_TRY(cudaDeviceGetAttribute(&shape.n_sm, cudaDevAttrMultiProcessorCount, dev));
-  shape.th = 16;   // mixed path default (FP64 always uses 32-row tiles)
+  shape.th = 0;    // 0: chosen per run
   P.resize(n);
   long long sites = 0;
   size_t slots = 0;
@@ -496,7 +525,7 @@ dirac_status Engine::run(vec4* const* psi, int nsteps, double dt, int m, double 
   if (a_xy)
     for (long long k = 0; k < 2LL * nsteps * np; ++k)
       if (!std::isfinite(a_xy[k])) return fail(DIRAC_EINVAL, "non-finite vector potential in the schedule");
-  const int th = precision == DIRAC_FP64 ? 32 : shape.th;
+  const int th = shape.th ? shape.th : (precision == DIRAC_FP64 ? fp64_tile_height(P, shape.n_sm) : 16);
   // tile list for this tile height
   int tt = 0;
   for (HostProblem& q : P) {
@@ -1056,7 +1085,7 @@ dirac_status dirac_batch_autotune(dirac_batch* bt, void* const* psi_dev, double 
   for (int b = 0; b < np; ++b) sp[b] = reinterpret_cast<vec4*>(scratch + off[b]);
   struct Cand { int th, cap; };
   std::vector<Cand> cands;
-  if (e.precision == DIRAC_FP64) cands = {{32, 0}, {32, 1}};
+  if (e.precision == DIRAC_FP64) cands = {{32, 0}, {16, 0}};
   else cands = {{16, 0}, {16, 4}, {32, 0}, {32, 2}};
   const LaunchShape keep = e.shape;
   const bool probe_keep = e.need_probe;

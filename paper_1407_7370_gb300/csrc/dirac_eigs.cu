@@ -122,8 +122,11 @@ __device__ __forceinline__ void load_site(const v4* __restrict__ in, int gx, int
 }
 
 // T = double: the FP64 product.  T = float: the mixed-precision product --
-// the stencil on FP32 copies of the vector (the diagonal as a float plus its
-// remainder), the Lanczos combination s_i y - c q^_{i-1} in FP64.
+// the off-diagonal part (differences and vector potential) on FP32 copies of
+// the vector, the diagonal (m c^2 + V - e0 and -m c^2 + V - e0) on the FP64
+// vector itself, so that the -2 m c^2 of the lower components adds no
+// u32 * 2 m c^2 rounding to the product; the Lanczos combination
+// s_i y - c q^_{i-1} in FP64.
 template <int R, bool DIRI, bool HAS_V, class T>
 __global__ void __launch_bounds__(256) eig_apply(const ApplyArgs a) {
   __shared__ double sh_nrm;
@@ -168,7 +171,10 @@ __global__ void __launch_bounds__(256) eig_apply(const ApplyArgs a) {
   if (x >= a.nx || y >= a.ny) return;
   const int nx = a.nx, ny = a.ny;
   T C[4], xp[4], xm[4], yp[4], ym[4], dxv[4], dyv[4];
-  load_site<DIRI>(a.in, x, y, nx, ny, C);
+  double C64[4];
+  load_site<DIRI>(a.in, x, y, nx, ny, C64);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) C[q] = (T)C64[q];
   load_site<DIRI>(a.in, x + 1, y, nx, ny, xp);
   load_site<DIRI>(a.in, x - 1, y, nx, ny, xm);
   load_site<DIRI>(a.in, x, y + 1, nx, ny, yp);
@@ -187,29 +193,24 @@ __global__ void __launch_bounds__(256) eig_apply(const ApplyArgs a) {
     }
   }
   const size_t idx = (size_t)y * nx + x;
-  const T au_hi = (T)a.au, ad_hi = (T)a.ad;
-  const T au_lo = (T)(a.au - (double)au_hi), ad_lo = (T)(a.ad - (double)ad_hi);
-  T au = au_hi, ad = ad_hi;
+  double au = a.au, ad = a.ad;
   if (HAS_V) {
-    const T v = (T)a.V[idx];
+    const double v = a.V[idx];
     au += v;
     ad += v;
   }
   const T kx = (T)a.kx, ky = (T)a.ky, cax = (T)a.cax, cay = (T)a.cay;
+  // off-diagonal part
   T ot[4];
-  // upper: (mc^2+V-e0) u + c[-i D_x d - D_y d + (A_x - i A_y) d]
-  ot[0] = au * C[0] + kx * dxv[3] - ky * dyv[2] + cax * C[2] + cay * C[3];
-  ot[1] = au * C[1] - kx * dxv[2] - ky * dyv[3] + cax * C[3] - cay * C[2];
-  // lower: (-mc^2+V-e0) d + c[-i D_x u + D_y u + (A_x + i A_y) u]
-  ot[2] = ad * C[2] + kx * dxv[1] + ky * dyv[0] + cax * C[0] - cay * C[1];
-  ot[3] = ad * C[3] - kx * dxv[0] + ky * dyv[1] + cax * C[1] + cay * C[0];
-  if constexpr (sizeof(T) == sizeof(float)) {
-    ot[0] = fma(au_lo, C[0], ot[0]);
-    ot[1] = fma(au_lo, C[1], ot[1]);
-    ot[2] = fma(ad_lo, C[2], ot[2]);
-    ot[3] = fma(ad_lo, C[3], ot[3]);
-  }
-  const double o[4] = {(double)ot[0], (double)ot[1], (double)ot[2], (double)ot[3]};
+  // upper: c[-i D_x d - D_y d + (A_x - i A_y) d]
+  ot[0] = kx * dxv[3] - ky * dyv[2] + cax * C[2] + cay * C[3];
+  ot[1] = -kx * dxv[2] - ky * dyv[3] + cax * C[3] - cay * C[2];
+  // lower: c[-i D_x u + D_y u + (A_x + i A_y) u]
+  ot[2] = kx * dxv[1] + ky * dyv[0] + cax * C[0] - cay * C[1];
+  ot[3] = -kx * dxv[0] + ky * dyv[1] + cax * C[1] + cay * C[0];
+  // plus the diagonal: (mc^2+V-e0) u and (-mc^2+V-e0) d
+  const double o[4] = {fma(au, C64[0], (double)ot[0]), fma(au, C64[1], (double)ot[1]),
+                       fma(ad, C64[2], (double)ot[2]), fma(ad, C64[3], (double)ot[3])};
   v4 r;
   if (csub != 0.0) {
     const v4 sv = a.sub[idx];

@@ -54,7 +54,6 @@ constexpr int KMAX = 32;        // Krylov dimension limit (one warp holds T)
 constexpr int CHEB_MAX = 160;   // Chebyshev terms limit
 constexpr int ERR_NONFINITE = 4;
 constexpr int TILE_W = 32;      // tile width in sites (one warp)
-constexpr int RPT = 4;          // rows per thread
 
 using vec4 = double4_32a;       // one site: (u.re, u.im, d.re, d.im)
 
@@ -139,6 +138,7 @@ struct LaunchParams {
   int chunk_q, chunk_r;     // tiles per CTA: q + 1 for the first r CTAs, then q
   int pass, m, probe;
   int conj_coef;            // 1: backward step (dt < 0): exp(+i H |dt|), the conjugate coefficients
+  int async_tiles;          // FP32 basis: stage passes >= 3 by asynchronous copies (many tiles per CTA)
   double mcc, dt, tol;      // dt = |dt|
   const int* step;          // step counter of the running call (index into fields)
 };
@@ -168,6 +168,16 @@ __device__ __forceinline__ int wrap(int g, int n, bool& outside) {
   outside = false;
   int r = g % n;
   return r < 0 ? r + n : r;
+}
+
+// asynchronous 16-byte global -> shared copy (bytes = 0: zero fill, nothing read)
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_wait() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
 // read-only (non-coherent) loads: the inputs of a pass are not written
@@ -362,7 +372,8 @@ __device__ inline void finish_pass(const LaunchParams& lp, const Problem* pr, in
 //
 // S    arithmetic type of the stencil (double: FP64 path; float: mixed path)
 // R    stencil half width (1: order 2, 2: order 4)
-// TH   tile height in sites (tiles are TILE_W x TH; TH / RPT warps per CTA)
+// TH   tile height in sites (tiles are TILE_W x TH; TH / RPT warps per tile
+//      worker, RPT rows per thread)
 //
 // Each problem runs its own next pass (DevState::cur_pass), so that a pass
 // can be re-run (see finish_pass) without the host knowing.  q^_{i-1} (and
@@ -376,6 +387,12 @@ __device__ inline void finish_pass(const LaunchParams& lp, const Problem* pr, in
 // ---------------------------------------------------------------------------
 template <class S, int TH, int SUB>
 __host__ __device__ constexpr int min_blocks() { return sizeof(S) == sizeof(float) ? (TH == 32 ? 4 : 8) : (SUB == 2 ? 1 : 2); }
+
+// rows per thread: four, except two on FP64 16-row tiles, which keep eight
+// warps per tile worker and halve the unit of work: a grid of a few tiles per
+// worker then ends with a shorter partial round
+template <class S, int TH>
+__host__ __device__ constexpr int rows_per_thread() { return (sizeof(S) == sizeof(double) && TH == 16) ? 2 : 4; }
 
 // tile workers per CTA: two on the FP64 path (one CTA per SM), one otherwise
 template <class S>
@@ -398,9 +415,11 @@ template <class S, int R, int TH, int SUB>
 __host__ __device__ constexpr size_t dyn_smem_bytes() { return SUB == 1 ? 0 : SUB * tile_bytes<S, R, TH>(); }
 
 template <class S, int R, int TH, bool DIRI, bool HAS_V>
-__global__ void __launch_bounds__(sub_workers<S>() * 32 * (TH / RPT), (min_blocks<S, TH, sub_workers<S>()>()))
+__global__ void __launch_bounds__(sub_workers<S>() * 32 * (TH / rows_per_thread<S, TH>()),
+                                  (min_blocks<S, TH, sub_workers<S>()>()))
 lanczos_pass(const __grid_constant__ LaunchParams lp) {
   using T4 = typename Vec4<S>::T;           // storage of y^ (and of q^ on the mixed path)
+  constexpr int RPT = rows_per_thread<S, TH>();
   constexpr int SUB = sub_workers<S>();     // tile workers
   constexpr int NG = TH / RPT;              // row groups = warps of a worker
   constexpr int NTS = 32 * NG;              // threads of a worker
@@ -426,6 +445,9 @@ lanczos_pass(const __grid_constant__ LaunchParams lp) {
   __shared__ __align__(32) S tile_s[SUB == 1 ? TH + 2 * R : 1][W][4];
   S(*const tile)[W][4] = SUB == 1 ? &tile_s[0]
                                   : reinterpret_cast<S(*)[W][4]>(dyn_smem + sub * tile_bytes<S, R, TH>());
+  // mixed path, passes >= 3: q^_{i-1} on the tile and halo, copied asynchronously
+  constexpr int NSQ = F32 ? (TH + 2 * R) * W : 1;
+  __shared__ __align__(16) float4 qbuf[NSQ];
   // barrier of this worker's threads (the whole CTA when there is one worker)
   auto sub_sync = [&]() {
     if constexpr (SUB == 1) {
@@ -506,34 +528,56 @@ lanczos_pass(const __grid_constant__ LaunchParams lp) {
     };
 
     S accP = S(0), accY = S(0), accX = S(0);
-    for (int tt = t + sub; tt < seg_end; tt += SUB) {
-      const int lt = tt - pr->tile_begin;
-      const int x0 = (lt % pr->tiles_x) * TILE_W;
-      const int y0 = (lt / pr->tiles_x) * TH;
-      S qprev[RPT][4];
+    // y^_i at one site from q^_i there (C) and its differences, q^_{i-1}
+    // (qp) and V; stores q^_i and y^_i and accumulates P, Y, X
+    auto site_update = [&](size_t idx, const S (&C)[4], const S (&dxv)[4], const S (&dyv)[4],
+                           const S (&qp)[4]) {
+      S au, ad;
+      if (HAS_V && Vp != nullptr) {   // V stored in S (float copy on the mixed path)
+        const S v = Vp[idx];
+        au = au_hi + v;
+        ad = ad_hi + v;
+      } else {
+        au = au_hi;
+        ad = ad_hi;
+      }
+      // C = (u.re, u.im, d.re, d.im); dxv/dyv likewise
+      S yv[4];
+      // upper: (mc^2+V-s-sigma) u + c[-i D_x d - D_y d + (A_x - i A_y) d]
+      yv[0] = au * C[0] + kx * dxv[3] - ky * dyv[2] + cAx * C[2] + cAy * C[3];
+      yv[1] = au * C[1] - kx * dxv[2] - ky * dyv[3] + cAx * C[3] - cAy * C[2];
+      // lower: (-mc^2+V-s-sigma) d + c[-i D_x u + D_y u + (A_x + i A_y) u]
+      yv[2] = ad * C[2] + kx * dxv[1] + ky * dyv[0] + cAx * C[0] - cAy * C[1];
+      yv[3] = ad * C[3] - kx * dxv[0] + ky * dyv[1] + cAx * C[1] + cAy * C[0];
+      if constexpr (F32) {
+        yv[0] = fma(au_lo, C[0], yv[0]);
+        yv[1] = fma(au_lo, C[1], yv[1]);
+        yv[2] = fma(ad_lo, C[2], yv[2]);
+        yv[3] = fma(ad_lo, C[3], yv[3]);
+      }
+      if (i >= 2) {
 #pragma unroll
-      for (int k = 0; k < RPT; ++k) {
-        const int r = tg + k * NG;
-        form(x0 + tx, y0 + r, r + R, tx + R, qprev[k]);
+        for (int q = 0; q < 4; ++q) yv[q] = fma(-eS, qp[q], yv[q]);
       }
-      constexpr int NH_ROW = 2 * R * TILE_W, NH = NH_ROW + 2 * R * TH;
-      for (int h = ltid; h < NH; h += NTS) {
-        int row, col;
-        if (h < NH_ROW) {               // rows above / below
-          const int r = h / TILE_W;
-          row = (r < R) ? r : TH + r;
-          col = (h % TILE_W) + R;
-        } else {                        // columns left / right
-          const int h2 = h - NH_ROW;
-          row = h2 / (2 * R) + R;
-          const int c = h2 % (2 * R);
-          col = (c < R) ? c : TILE_W + c;
+      if (!lp.probe) {
+        if (q_out) {
+          T4 o; o.x = C[0]; o.y = C[1]; o.z = C[2]; o.w = C[3];
+          static_cast<T4*>(q_out)[idx] = o;
         }
-        S dummy[4];
-        form(x0 + col - R, y0 + row - R, row, col, dummy);
+        if (y_out) {
+          T4 o; o.x = yv[0]; o.y = yv[1]; o.z = yv[2]; o.w = yv[3];
+          static_cast<T4*>(y_out)[idx] = o;
+        }
       }
-      sub_sync();
-
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        accP = fma(C[q], yv[q], accP);
+        accY = fma(yv[q], yv[q], accY);
+        accX = fma(C[q], C[q], accX);
+      }
+    };
+    // the stencil on the formed tile; qprev(k, r, c) gives q^_{i-1} of row k
+    auto stencil_rows = [&](int x0, int y0, auto&& qprev) {
 #pragma unroll
       for (int k = 0; k < RPT; ++k) {
         const int ry = tg + k * NG;
@@ -541,7 +585,7 @@ lanczos_pass(const __grid_constant__ LaunchParams lp) {
         if (x < nx && y < ny) {
           const size_t idx = (size_t)y * nx + x;
           const int r = ry + R, c = tx + R;
-          S C[4], dxv[4], dyv[4];
+          S C[4], dxv[4], dyv[4], qp[4];
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             C[q] = tile[r][c][q];
@@ -552,52 +596,85 @@ lanczos_pass(const __grid_constant__ LaunchParams lp) {
               dyv[q] = fma(S(8), dyv[q], tile[r - 2][c][q] - tile[r + 2][c][q]);
             }
           }
-          S au, ad;
-          if (HAS_V && Vp != nullptr) {   // V stored in S (float copy on the mixed path)
-            const S v = Vp[idx];
-            au = au_hi + v;
-            ad = ad_hi + v;
-          } else {
-            au = au_hi;
-            ad = ad_hi;
-          }
-          // C = (u.re, u.im, d.re, d.im); dxv/dyv likewise
-          S yv[4];
-          // upper: (mc^2+V-s-sigma) u + c[-i D_x d - D_y d + (A_x - i A_y) d]
-          yv[0] = au * C[0] + kx * dxv[3] - ky * dyv[2] + cAx * C[2] + cAy * C[3];
-          yv[1] = au * C[1] - kx * dxv[2] - ky * dyv[3] + cAx * C[3] - cAy * C[2];
-          // lower: (-mc^2+V-s-sigma) d + c[-i D_x u + D_y u + (A_x + i A_y) u]
-          yv[2] = ad * C[2] + kx * dxv[1] + ky * dyv[0] + cAx * C[0] - cAy * C[1];
-          yv[3] = ad * C[3] - kx * dxv[0] + ky * dyv[1] + cAx * C[1] + cAy * C[0];
-          if constexpr (F32) {
-            yv[0] = fma(au_lo, C[0], yv[0]);
-            yv[1] = fma(au_lo, C[1], yv[1]);
-            yv[2] = fma(ad_lo, C[2], yv[2]);
-            yv[3] = fma(ad_lo, C[3], yv[3]);
-          }
-          if (i >= 2) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) yv[q] = fma(-eS, qprev[k][q], yv[q]);
-          }
-          if (!lp.probe) {
-            if (q_out) {
-              T4 o; o.x = C[0]; o.y = C[1]; o.z = C[2]; o.w = C[3];
-              static_cast<T4*>(q_out)[idx] = o;
-            }
-            if (y_out) {
-              T4 o; o.x = yv[0]; o.y = yv[1]; o.z = yv[2]; o.w = yv[3];
-              static_cast<T4*>(y_out)[idx] = o;
-            }
-          }
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            accP = fma(C[q], yv[q], accP);
-            accY = fma(yv[q], yv[q], accY);
-            accX = fma(C[q], C[q], accX);
-          }
+          qprev(k, r, c, qp);
+          site_update(idx, C, dxv, dyv, qp);
         }
       }
-      sub_sync();   // the tile buffer is reused next
+    };
+
+    bool done_async = false;
+    if constexpr (F32) {
+     if (!q64 && lp.async_tiles) {
+      done_async = true;
+      // mixed path, passes >= 3: y^_{i-1} and q^_{i-1} of the tile and its
+      // halo (a full rectangle) go to shared memory by asynchronous copies,
+      // all in flight at once and without registers; q^_i is formed in place
+      constexpr int NS = (TH + 2 * R) * W;
+      float4* const tf = reinterpret_cast<float4*>(&tile[0][0][0]);
+      const float4* const qsrc = static_cast<const float4*>(q_prev);
+      for (int tt = t; tt < seg_end; ++tt) {
+        const int lt = tt - pr->tile_begin;
+        const int x0 = (lt % pr->tiles_x) * TILE_W;
+        const int y0 = (lt / pr->tiles_x) * TH;
+        for (int e = threadIdx.x; e < NS; e += NT) {
+          const int r = e / W, c = e - r * W;
+          bool ox, oy;
+          const int ix = wrap<DIRI>(x0 - R + c, nx, ox), iy = wrap<DIRI>(y0 - R + r, ny, oy);
+          const bool in = !(ox || oy);
+          const size_t idx = in ? (size_t)iy * nx + ix : 0;
+          cp_async16(tf + e, reinterpret_cast<const float4*>(yprev) + idx, in ? 16 : 0);
+          cp_async16(qbuf + e, qsrc + idx, in ? 16 : 0);
+        }
+        cp_async_commit_wait();
+        __syncthreads();
+        for (int e = threadIdx.x; e < NS; e += NT) {
+          const float4 yv = tf[e], qp = qbuf[e];
+          tf[e] = make_float4(fmaf(-(float)gdS, qp.x, (float)gS * yv.x), fmaf(-(float)gdS, qp.y, (float)gS * yv.y),
+                              fmaf(-(float)gdS, qp.z, (float)gS * yv.z), fmaf(-(float)gdS, qp.w, (float)gS * yv.w));
+        }
+        __syncthreads();
+        stencil_rows(x0, y0, [&](int, int r, int c, S (&qp)[4]) {
+          const float4 v = qbuf[r * W + c];
+          qp[0] = (S)v.x; qp[1] = (S)v.y; qp[2] = (S)v.z; qp[3] = (S)v.w;
+        });
+        __syncthreads();   // tile and qbuf are reused next
+      }
+     }
+    }
+    if (!done_async) {
+      for (int tt = t + sub; tt < seg_end; tt += SUB) {
+        const int lt = tt - pr->tile_begin;
+        const int x0 = (lt % pr->tiles_x) * TILE_W;
+        const int y0 = (lt / pr->tiles_x) * TH;
+        S qprev[RPT][4];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+          const int r = tg + k * NG;
+          form(x0 + tx, y0 + r, r + R, tx + R, qprev[k]);
+        }
+        constexpr int NH_ROW = 2 * R * TILE_W, NH = NH_ROW + 2 * R * TH;
+        for (int h = ltid; h < NH; h += NTS) {
+          int row, col;
+          if (h < NH_ROW) {               // rows above / below
+            const int r = h / TILE_W;
+            row = (r < R) ? r : TH + r;
+            col = (h % TILE_W) + R;
+          } else {                        // columns left / right
+            const int h2 = h - NH_ROW;
+            row = h2 / (2 * R) + R;
+            const int c = h2 % (2 * R);
+            col = (c < R) ? c : TILE_W + c;
+          }
+          S dummy[4];
+          form(x0 + col - R, y0 + row - R, row, col, dummy);
+        }
+        sub_sync();
+        stencil_rows(x0, y0, [&](int k, int, int, S (&qp)[4]) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) qp[q] = qprev[k][q];
+        });
+        sub_sync();   // the tile buffer is reused next
+      }
     }
     t = seg_end;
 

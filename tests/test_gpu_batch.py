@@ -57,6 +57,8 @@ def _problem(k, g):
 
 @pytest.mark.parametrize("precision,order,boundary,th", [("fp64", 2, "periodic", 32),
                                                           ("fp64", 4, "dirichlet", 32),
+                                                          ("fp64", 2, "periodic", 16),
+                                                          ("fp64", 4, "dirichlet", 16),
                                                           ("mixed", 2, "periodic", 32),
                                                           ("mixed", 2, "periodic", 16),
                                                           ("mixed", 4, "dirichlet", 16)])
@@ -64,8 +66,7 @@ def test_batch_matches_oracle_per_problem(precision, order, boundary, th):
     from paper_1407_7370_gb300 import BatchPropagator
     dt, m, steps = 1e-4, 8, 4
     bp = BatchPropagator(GRIDS, order=order, boundary=boundary, m_max=m, precision=precision)
-    if precision == "mixed":
-        bp.set_launch_shape(th)
+    bp.set_launch_shape(th)
     probs = [_problem(k, g) for k, g in enumerate(GRIDS)]
     rng = np.random.default_rng(7)
     A = rng.uniform(-20, 20, size=(steps, len(GRIDS), 2))

@@ -263,9 +263,13 @@ def test_eigs_launch_count_and_kernel_timing():
 
 
 def test_eigs_mixed_stencil_close_to_fp64():
-    """FP32 stencil products with FP64 reorthogonalisation and Ritz values:
-    the eigenvalues move by about u32 times the size of (H - s) on the
-    states (their lower components carry the -2 m c^2 diagonal)."""
+    """FP32 off-diagonal stencil products (FP64 diagonal, FP64
+    reorthogonalisation and Ritz values): each product carries a rounding
+    error of a few u32 times ||K|| ||q||, K = c sigma.(p + A) the part done in
+    FP32, so the Ritz values move by at most that much, plus the looser
+    convergence tolerance.  The grid is small enough for the whole spectrum
+    of the discrete operator (dense matrix, LAPACK), which has a close
+    quadruplet near -2.03 au: the looser tolerance admits the inner pair."""
     g, V, start = soft_core_case(24, 20, 0.3, 2.0)
     window = (-C * C, 0.0)
     p64, op = make(g, V=V, shift=C * C)
@@ -273,7 +277,11 @@ def test_eigs_mixed_stencil_close_to_fp64():
     r64 = p64.eigs(dev(start), n_want=64, max_iter=150, tol=1e-9, window=window)
     r32 = p32.eigs(dev(start), n_want=64, max_iter=150, tol=1e-6, window=window)
     assert r32.values.size >= 2
-    ref = lz.lanczos_eigs(op, start, n_want=64, max_iter=150, tol=1e-9, window=window)
-    for v in r32.values:
-        assert np.min(np.abs(ref.values - v)) <= 1e-5 * max(1.0, abs(v))
-    assert np.max(np.abs(r64.values - ref.values[: r64.values.size])) <= 1e-11 * norm_a(op)
+    exact = np.linalg.eigvalsh(ham.dense(op))
+    exact = exact[(exact > window[0]) & (exact < window[1])]
+    kin = op.c * (np.sqrt(2.0) / min(op.dx, op.dy) + abs(op.A[0]) + abs(op.A[1]))
+    for v, b in zip(r32.values, r32.bounds):
+        assert np.min(np.abs(exact - v)) <= 4 * 2.0 ** -24 * kin + 2 * b, (v, b)
+    assert r64.values.size >= 2
+    for v in r64.values:
+        assert np.min(np.abs(exact - v)) <= 1e-11 * norm_a(op)
