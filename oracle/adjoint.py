@@ -123,6 +123,30 @@ def gradient(op: ham.Operator, psi0: np.ndarray, dt: float, A_steps, kind: str,
     return Gradient(L, dV, dA)
 
 
+def jvp(op: ham.Operator, psi0: np.ndarray, dt: float, A_steps, kind: str, phi=None,
+        dV=None, dA=None):
+    """(L, directional derivative of L along (dV, dA)) in one forward-mode
+    sweep: dV a field (ny, nx) added to V, dA (nsteps, 2) added to the step
+    means; the step's derivative is the Frechet derivative of the exponential
+    in the direction E_n = diag(dV) + dA_n . (dH/dA)."""
+    A_steps = np.asarray(A_steps, dtype=float)
+    Xs = _generators(op, A_steps, dt)
+    n2 = 2 * op.nx * op.ny
+    ev = np.zeros(n2) if dV is None else np.repeat(np.asarray(dV, dtype=float).reshape(-1), 2)
+    ax, ay = _a_direction(op, 0), _a_direction(op, 1)
+    psi = psi0.reshape(-1).astype(np.complex128)
+    dpsi = np.zeros_like(psi)
+    for n, X in enumerate(Xs):
+        E = np.diag(ev).astype(np.complex128)
+        if dA is not None:
+            E = E + dA[n, 0] * ax + dA[n, 1] * ay
+        U, F = scipy.linalg.expm_frechet(X, -1j * dt * E)
+        dpsi = U @ dpsi + F @ psi
+        psi = U @ psi
+    L, lam = observable(kind, op, psi.reshape(psi0.shape), phi)
+    return L, 2.0 * np.vdot(lam.reshape(-1), dpsi).real
+
+
 def fd_gradient_V(op, psi0, dt, A_steps, kind, phi, site: int, h: float) -> float:
     """Central finite difference of L in V at one site (step h)."""
     def L_at(dv):
@@ -149,5 +173,5 @@ def sine_basis_means(nsteps: int, dt: float, n_coef: int, duration: float) -> np
     return (np.cos(w * t0) - np.cos(w * (t0 + dt))) / (w * dt)
 
 
-__all__ = ["momentum_x", "observable", "forward", "loss", "gradient", "Gradient",
+__all__ = ["momentum_x", "observable", "forward", "loss", "gradient", "Gradient", "jvp",
            "fd_gradient_V", "fd_gradient_A", "sine_basis_means"]

@@ -69,6 +69,31 @@ def test_adjoint_matches_oracle_per_site_and_step(kind):
     assert np.max(np.abs(res.dA - ref.dA)) <= 1e-9 * np.max(np.abs(ref.dA))
 
 
+@pytest.mark.parametrize("kind,order,boundary", [("px", 2, "periodic"), ("proj", 4, "dirichlet"),
+                                                 ("px", 4, "dirichlet")])
+def test_adjoint_contracted_with_random_direction_matches_oracle_jvp(kind, order, boundary):
+    """A 40x20 grid (several warps and blocks per row, ragged in both
+    directions), where the oracle runs one forward-mode sweep along a random
+    direction instead of one per site: the GPU's reverse-mode gradient
+    contracted with that direction must give the same derivative."""
+    g, op, psi0, phi, A = small_case(40, 20, 0.3, nsteps=3)
+    op = ham.Operator(g.nx, g.ny, g.dx, g.dy, order=order,
+                      boundary=ham.DIRICHLET if boundary == "dirichlet" else ham.PERIODIC,
+                      V=op.V, shift=C * C)
+    dt = 2e-5
+    rng = np.random.default_rng(5)
+    dV = rng.standard_normal((g.ny, g.nx))
+    dA = rng.standard_normal(A.shape)
+    p = gpu_prop(g, op.V, order=order, boundary=boundary)
+    res = p.adjoint_gradient(dev(psi0), A.shape[0], dt, 16, A, observable=kind, phi=dev(phi),
+                             checkpoint_every=2)
+    L, d_ref = adj.jvp(op, psi0, dt, A, kind, phi, dV=dV, dA=dA)
+    d_gpu = float(np.sum(res.dV.cpu().numpy() * dV) + np.sum(res.dA * dA))
+    scale = float(np.sum(np.abs(res.dV.cpu().numpy() * dV)) + np.sum(np.abs(res.dA * dA)))
+    assert abs(res.loss - L) <= 1e-12 * abs(L)
+    assert abs(d_gpu - d_ref) <= 1e-10 * scale, (d_gpu, d_ref, scale)
+
+
 def test_adjoint_blocks_and_pulse_coefficients_match_oracle():
     g, op, psi0, phi, A = small_case(8, 6, 0.35, nsteps=5)
     dt = 2e-5

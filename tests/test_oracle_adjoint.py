@@ -48,6 +48,26 @@ def test_gradient_matches_central_differences(kind):
 
 
 @pytest.mark.parametrize("kind", ["px", "proj"])
+def test_directional_derivative_matches_central_differences(kind):
+    """One forward-mode sweep along a random (dV, dA) against the central
+    difference of the forward map along the same direction."""
+    op, psi0, phi, A = small_case()
+    dt = 2e-4
+    rng = np.random.default_rng(11)
+    dV = rng.standard_normal((op.ny, op.nx))
+    dA = rng.standard_normal(A.shape)
+    L, d = adj.jvp(op, psi0, dt, A, kind, phi, dV=dV, dA=dA)
+    h = 1e-4
+
+    def L_at(e):
+        o = dataclasses.replace(op, V=op.V + e * dV)
+        return adj.loss(o, psi0, dt, A + e * dA, kind, phi)
+    fd = (L_at(h) - L_at(-h)) / (2 * h)
+    assert abs(L - adj.loss(op, psi0, dt, A, kind, phi)) <= 1e-13 * abs(L)
+    assert abs(d - fd) <= 1e-6 * max(abs(fd), 1e-3 * abs(L)), (d, fd)
+
+
+@pytest.mark.parametrize("kind", ["px", "proj"])
 def test_uniform_potential_changes_only_the_phase(kind):
     op, psi0, phi, A = small_case()
     g = adj.gradient(op, psi0, 2e-4, A, kind, phi)
