@@ -52,8 +52,10 @@ def kernel_sha() -> str:
     return hashlib.sha1(open(path, "rb").read()).hexdigest()[:12]
 
 
-def traffic_for(prec: str):
+def traffic_for(prec: str, grid):
     rec = TRAFFIC.get(prec)
+    if grid.n_sites != CFG["grid"].n_sites:   # captured on the configured grid only
+        return None
     if rec and rec[0] == kernel_sha():
         return rec[1]
     return None
@@ -73,7 +75,11 @@ def parse():
                     help="grid side of the eigen workload (default: the configured 2048)")
     ap.add_argument("--eigen-iters", type=int, default=None, help="Lanczos iterations of the eigen workload")
     ap.add_argument("--adjoint-steps", type=int, default=None, help="steps of the adjoint workload")
-    ap.add_argument("--only", choices=["fp64", "mixed", "eigen", "adjoint"], default=None,
+    ap.add_argument("--side", type=int, default=None,
+                    help="grid side of the laser-packet workload (profiling; default: the configured 1024)")
+    ap.add_argument("--batch-compare-steps", type=int, default=None,
+                    help="steps of the batched mixed-vs-FP64 comparison (profiling; default: the configured 2000)")
+    ap.add_argument("--only", choices=["fp64", "mixed", "eigen", "adjoint", "batch"], default=None,
                     help="run one path only (for profiling); prints a partial line")
     return ap.parse_args()
 
@@ -271,7 +277,7 @@ def measure_batch(args, torch, world, dist, gi, pk):
     W = args.warmup
     K = max(5, min(args.steps, 60))
     K64 = max(3, K // 12)
-    KC = cfg["steps"]             # the mixed-vs-FP64 comparison runs the whole configured length
+    KC = args.batch_compare_steps or cfg["steps"]   # the comparison runs the whole configured length
     C2 = 137.036 ** 2             # energy shift m c^2 (positive-energy packets)
     tot = max(W + 2 * K + 8, KC)
     base = np.array([pulse_sin2_mean(k * dt, dt, 1.0, cfg["pulse"].omega, cfg["pulse"].duration)
@@ -525,17 +531,21 @@ def run_ours(args):
     from paper_1407_7370_gb300.propagator import pulse_schedule
 
     g, m, dt, pulse = CFG["grid"], CFG["m"], CFG["dt"], CFG["pulse"]
+    if args.side:
+        g = wl.Grid(args.side, args.side, g.dx, g.dy)
     psi0 = wl.positive_energy_packet(g, p0=CFG["p0"], sigma_x=CFG["sigma_x"])
     K, W = args.steps, args.warmup
     A = pulse_schedule(0.0, dt, W + 2 * K, pulse.a0, pulse.omega, pulse.duration)
     pk = peaks()
     hbm_peak = pk.get("hbm_gbs", 6800.0)
     hbm_src = "MEASURED_PEAKS.json hbm_gbs (burst copy)" if "hbm_gbs" in pk else "fallback 6.8 TB/s"
-    if args.only in ("eigen", "adjoint"):   # one workload alone (profiling runs)
+    if args.only in ("eigen", "adjoint", "batch"):   # one workload alone (profiling runs)
         if args.only == "eigen":
             r = measure_eigen(torch, local, pk, args.eigen_side, args.eigen_iters)
-        else:
+        elif args.only == "adjoint":
             r = measure_adjoint(torch, local, pk, args.adjoint_steps)
+        else:
+            r = measure_batch(args, torch, world, dist, local, pk)
         if rank == 0:
             print(json.dumps({"partial": args.only, "result": r}), flush=True)
         return 0
@@ -571,7 +581,7 @@ def run_ours(args):
     fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12   # TFLOP/s, see the design doc
     flops = PASS_FLOPS_PER_SITE * g.n_sites / f_pass / 1e12
     roofline = {"bound": "alu", "achieved": flops, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": flops / fp64_peak, "traffic": traffic_for("fp64"),
+                "frac": flops / fp64_peak, "traffic": traffic_for("fp64", g),
                 "kernel": "lanczos_pass<double>", "kernel_avg_us": f_pass * 1e6,
                 "kernel_share": f_share,
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz "
@@ -586,7 +596,7 @@ def run_ours(args):
     mixed = {"value": site_rate(x["t"], K), "unit": UNIT, "ms_per_step": 1e3 * x["t"] / K,
              "dtype": "f32 stencil/basis + f64 scalars and state",
              "roofline": {"bound": "hbm", "achieved": x_gbs, "peak": hbm_peak, "unit": "GB/s",
-                          "frac": x_gbs / hbm_peak, "traffic": traffic_for("mixed"),
+                          "frac": x_gbs / hbm_peak, "traffic": traffic_for("mixed", g),
                           "kernel": "lanczos_pass<float>", "kernel_avg_us": x_pass * 1e6,
                           "kernel_share": x_share, "peak_source": hbm_src,
                           "bytes_per_site": PASS_BYTES_PER_SITE_MIXED},
