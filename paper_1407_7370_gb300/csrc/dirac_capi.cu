@@ -163,7 +163,7 @@ struct LaunchShape {
 #endif
 constexpr int ASYNC_MIN_TILES = DIRAC_ASYNC_MIN_TILES;
 
-template <class S, int R, int TH, bool D, bool V>
+template <class S, int R, int TH, bool D, bool V, bool AY>
 cudaError_t launch_pass_t(LaunchParams p, const LaunchShape& ls, cudaStream_t s) {
   static int occ = 0;
   constexpr int NT = sub_workers<S>() * 32 * (TH / rows_per_thread<S, TH>());
@@ -171,11 +171,11 @@ cudaError_t launch_pass_t(LaunchParams p, const LaunchShape& ls, cudaStream_t s)
   if (occ == 0) {
     cudaError_t e = cudaSuccess;
     if (smem > 0) {
-      e = cudaFuncSetAttribute(lanczos_pass<S, R, TH, D, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(lanczos_pass<S, R, TH, D, V, AY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem);
       if (e != cudaSuccess) return e;
     }
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lanczos_pass<S, R, TH, D, V>, NT, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lanczos_pass<S, R, TH, D, V, AY>, NT, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
   }
@@ -187,18 +187,29 @@ cudaError_t launch_pass_t(LaunchParams p, const LaunchShape& ls, cudaStream_t s)
   // asynchronous tile staging pays once each CTA has several tiles to stream
   // (a grid much larger than L2 holds); below that the extra barrier costs more
   p.async_tiles = p.chunk_q >= ASYNC_MIN_TILES;
-  return launch_pdl(lanczos_pass<S, R, TH, D, V>, grid, NT, smem, s, p);
+  return launch_pdl(lanczos_pass<S, R, TH, D, V, AY>, grid, NT, smem, s, p);
+}
+
+// FP64: a kernel without the c A_y terms (four FMAs per site of ~54) when no
+// step of the launch has A_y != 0 (linear polarisation along x, static
+// fields); the FP32 pass, bound by memory, keeps one kernel
+template <class S, int R, int TH, bool D, bool V>
+cudaError_t launch_pass_ay(const LaunchParams& p, const LaunchShape& ls, cudaStream_t s) {
+  if constexpr (sizeof(S) == sizeof(double)) {
+    if (!p.has_ay) return launch_pass_t<S, R, TH, D, V, false>(p, ls, s);
+  }
+  return launch_pass_t<S, R, TH, D, V, true>(p, ls, s);
 }
 
 template <class S, int TH>
 cudaError_t launch_pass_s(int order, bool diri, bool hasv, const LaunchParams& p, const LaunchShape& ls,
                           cudaStream_t s) {
   if (order == 2) {
-    if (diri) return hasv ? launch_pass_t<S, 1, TH, true, true>(p, ls, s) : launch_pass_t<S, 1, TH, true, false>(p, ls, s);
-    return hasv ? launch_pass_t<S, 1, TH, false, true>(p, ls, s) : launch_pass_t<S, 1, TH, false, false>(p, ls, s);
+    if (diri) return hasv ? launch_pass_ay<S, 1, TH, true, true>(p, ls, s) : launch_pass_ay<S, 1, TH, true, false>(p, ls, s);
+    return hasv ? launch_pass_ay<S, 1, TH, false, true>(p, ls, s) : launch_pass_ay<S, 1, TH, false, false>(p, ls, s);
   }
-  if (diri) return hasv ? launch_pass_t<S, 2, TH, true, true>(p, ls, s) : launch_pass_t<S, 2, TH, true, false>(p, ls, s);
-  return hasv ? launch_pass_t<S, 2, TH, false, true>(p, ls, s) : launch_pass_t<S, 2, TH, false, false>(p, ls, s);
+  if (diri) return hasv ? launch_pass_ay<S, 2, TH, true, true>(p, ls, s) : launch_pass_ay<S, 2, TH, true, false>(p, ls, s);
+  return hasv ? launch_pass_ay<S, 2, TH, false, true>(p, ls, s) : launch_pass_ay<S, 2, TH, false, false>(p, ls, s);
 }
 
 // FP64 path: everything complex128.  Mixed path: complex64 basis (passes 1
@@ -593,10 +604,12 @@ dirac_status Engine::run(vec4* const* psi, int nsteps, double dt, int m, double 
     d.probe_coef = make_coef(1.0, 0.0, 0.0, mcc - q.shift, -mcc - q.shift);
     hasv = hasv || q.has_v;
   }
+  bool has_ay = false;
   for (int k = 0; k < nfield; ++k) {
     const int b = k % np;
     const double ax = a_xy ? a_xy[2 * (size_t)k] : P[b].ax;
     const double ay = a_xy ? a_xy[2 * (size_t)k + 1] : P[b].ay;
+    has_ay = has_ay || ay != 0.0;
     FieldStep& f = hf[k];
     f.cAx = c * ax;   // electron: p - qA = p + A
     f.cAy = c * ay;
@@ -621,6 +634,7 @@ dirac_status Engine::run(vec4* const* psi, int nsteps, double dt, int m, double 
   lp.mcc = mcc;
   lp.dt = dt;
   lp.conj_coef = backward ? 1 : 0;
+  lp.has_ay = has_ay ? 1 : 0;
   lp.tol = tol;
   lp.step = d_step;
   lp.redo_budget = redo_budget(precision, m);
@@ -1314,6 +1328,7 @@ extern "C" dirac_status dirac_lanczos_step_noalloc(const dirac_problem* pb, void
   lp.fstride = 0;
   lp.nprob = 1;
   lp.total_tiles = ntiles;
+  lp.has_ay = pb->A_y != 0.0 ? 1 : 0;
   lp.m = m;
   lp.mcc = mcc;
   lp.dt = dt;

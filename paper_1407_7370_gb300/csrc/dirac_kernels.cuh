@@ -139,6 +139,7 @@ struct LaunchParams {
   int pass, m, probe;
   int conj_coef;            // 1: backward step (dt < 0): exp(+i H |dt|), the conjugate coefficients
   int async_tiles;          // FP32 basis: stage passes >= 3 by asynchronous copies (many tiles per CTA)
+  int has_ay;               // 0: A_y = 0 in every step and problem (host: picks the kernel)
   double mcc, dt, tol;      // dt = |dt|
   const int* step;          // step counter of the running call (index into fields)
 };
@@ -414,7 +415,7 @@ __device__ __forceinline__ int cta_of_tile(int t, int q, int r) {
 template <class S, int R, int TH, int SUB>
 __host__ __device__ constexpr size_t dyn_smem_bytes() { return SUB == 1 ? 0 : SUB * tile_bytes<S, R, TH>(); }
 
-template <class S, int R, int TH, bool DIRI, bool HAS_V>
+template <class S, int R, int TH, bool DIRI, bool HAS_V, bool HAS_AY>
 __global__ void __launch_bounds__(sub_workers<S>() * 32 * (TH / rows_per_thread<S, TH>()),
                                   (min_blocks<S, TH, sub_workers<S>()>()))
 lanczos_pass(const __grid_constant__ LaunchParams lp) {
@@ -544,11 +545,17 @@ lanczos_pass(const __grid_constant__ LaunchParams lp) {
       // C = (u.re, u.im, d.re, d.im); dxv/dyv likewise
       S yv[4];
       // upper: (mc^2+V-s-sigma) u + c[-i D_x d - D_y d + (A_x - i A_y) d]
-      yv[0] = au * C[0] + kx * dxv[3] - ky * dyv[2] + cAx * C[2] + cAy * C[3];
-      yv[1] = au * C[1] - kx * dxv[2] - ky * dyv[3] + cAx * C[3] - cAy * C[2];
+      yv[0] = au * C[0] + kx * dxv[3] - ky * dyv[2] + cAx * C[2];
+      yv[1] = au * C[1] - kx * dxv[2] - ky * dyv[3] + cAx * C[3];
       // lower: (-mc^2+V-s-sigma) d + c[-i D_x u + D_y u + (A_x + i A_y) u]
-      yv[2] = ad * C[2] + kx * dxv[1] + ky * dyv[0] + cAx * C[0] - cAy * C[1];
-      yv[3] = ad * C[3] - kx * dxv[0] + ky * dyv[1] + cAx * C[1] + cAy * C[0];
+      yv[2] = ad * C[2] + kx * dxv[1] + ky * dyv[0] + cAx * C[0];
+      yv[3] = ad * C[3] - kx * dxv[0] + ky * dyv[1] + cAx * C[1];
+      if constexpr (HAS_AY) {   // else A_y = 0 in every step of the launch
+        yv[0] = fma(cAy, C[3], yv[0]);
+        yv[1] = fma(-cAy, C[2], yv[1]);
+        yv[2] = fma(-cAy, C[1], yv[2]);
+        yv[3] = fma(cAy, C[0], yv[3]);
+      }
       if constexpr (F32) {
         yv[0] = fma(au_lo, C[0], yv[0]);
         yv[1] = fma(au_lo, C[1], yv[1]);
