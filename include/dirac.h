@@ -169,10 +169,12 @@ long long dirac_kernel_launches(const dirac_ctx* ctx);
  * for the last recorded event and returns, per kernel kind, the device time
  * (ms) between each kernel's event and the next one, and the number of
  * launches, accumulated since the previous read; it then clears the record.
- * Kinds: 0 = Lanczos pass (stencil + reductions), 1 = recombination.
+ * Kinds: 0 = Lanczos pass (stencil + reductions), 1 = recombination,
+ * 2 = one-launch time step (all passes and the recombination, see
+ * dirac_set_step_mode).
  * ms and launches point to DIRAC_KERNEL_KINDS elements each.
  */
-#define DIRAC_KERNEL_KINDS 2
+#define DIRAC_KERNEL_KINDS 3
 dirac_status dirac_profile_enable(dirac_ctx* ctx, int enable);
 dirac_status dirac_profile_read(dirac_ctx* ctx, double* ms, long long* launches);
 
@@ -251,6 +253,26 @@ dirac_status dirac_batch_autotune(dirac_batch* batch, void* const* psi_dev, doub
  */
 dirac_status dirac_batch_use_graphs(dirac_batch* batch, int enable);
 dirac_status dirac_use_graphs(dirac_ctx* ctx, int enable);
+
+/*
+ * How the time steps of a context are launched.
+ *   DIRAC_STEP_PASSES: one launch per Lanczos pass and one for the
+ *     recombination (replayed as a CUDA graph); the last CTA of each pass
+ *     updates the scalars.
+ *   DIRAC_STEP_ONE_LAUNCH: the whole step as one cooperative launch (every
+ *     CTA resident), the passes separated by grid-wide barriers; after each
+ *     barrier every CTA sums all CTA partials in the same order and updates
+ *     its own copy of the scalars.  Each barrier wait is bounded: a timeout
+ *     ends the launch and the next read of the state reports DIRAC_ECUDA.
+ *   DIRAC_STEP_AUTO (default): one launch per step on the FP64 path (one
+ *     CTA per SM), per-pass launches on the mixed path (eight CTAs per SM,
+ *     where the barrier costs more than the launch boundaries).
+ * Results agree to rounding: the partial sums are added in another order.
+ */
+#define DIRAC_STEP_AUTO 0
+#define DIRAC_STEP_PASSES 1
+#define DIRAC_STEP_ONE_LAUNCH 2
+dirac_status dirac_set_step_mode(dirac_ctx* ctx, int mode);
 
 /* dirac_profile_enable / dirac_profile_read / dirac_kernel_launches for a batch. */
 dirac_status dirac_batch_profile_enable(dirac_batch* batch, int enable);

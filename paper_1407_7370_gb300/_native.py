@@ -15,7 +15,7 @@ _lib = None
 
 HEADER = os.path.join(_build.ROOT, "include", "dirac.h")
 KRYLOV_MAX = 32
-KERNEL_KINDS = 2
+KERNEL_KINDS = 3
 EIG_RITZ_MAX = 256
 EIG_ITER_MAX = 8192
 
@@ -23,6 +23,7 @@ OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ESTATE = range(6)
 PERIODIC, DIRICHLET = 0, 1
 FP64, MIXED = 0, 1
 OBS_PX, OBS_PROJ = 0, 1
+STEP_AUTO, STEP_PASSES, STEP_ONE_LAUNCH = 0, 1, 2
 
 
 class StepInfoC(ctypes.Structure):
@@ -125,6 +126,7 @@ def lib():
         "dirac_batch_autotune": (i, [vp, ctypes.POINTER(vp), d, i, dp, i, ctypes.POINTER(TuneResultC)]),
         "dirac_batch_use_graphs": (i, [vp, i]),
         "dirac_use_graphs": (i, [vp, i]),
+        "dirac_set_step_mode": (i, [vp, i]),
         "dirac_profile_read": (i, [vp, dp, ctypes.POINTER(ctypes.c_longlong)]),
         "dirac_apply_hamiltonian": (i, [vp, vp, vp]),
         "dirac_lanczos_eigs": (i, [vp, vp, i, i, i, d, d, d, i, i, d, dp, dp, vp,

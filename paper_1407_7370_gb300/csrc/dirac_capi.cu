@@ -158,11 +158,6 @@ struct LaunchShape {
 // Persistent launch: as many CTAs as are resident at once (at most one per
 // tile), each taking a contiguous chunk of the tile list whose size differs
 // from the others' by at most one tile.
-#ifndef DIRAC_ASYNC_MIN_TILES
-#define DIRAC_ASYNC_MIN_TILES 4
-#endif
-constexpr int ASYNC_MIN_TILES = DIRAC_ASYNC_MIN_TILES;
-
 template <class S, int R, int TH, bool D, bool V, bool AY>
 cudaError_t launch_pass_t(LaunchParams p, const LaunchShape& ls, cudaStream_t s) {
   static int occ = 0;
@@ -184,8 +179,6 @@ cudaError_t launch_pass_t(LaunchParams p, const LaunchShape& ls, cudaStream_t s)
   const int grid = std::max(1, std::min(p.total_tiles, slots));
   p.chunk_q = p.total_tiles / grid;
   p.chunk_r = p.total_tiles % grid;
-  // asynchronous tile staging pays once each CTA has several tiles to stream
-  // (a grid much larger than L2 holds); below that the extra barrier costs more
   p.async_tiles = p.chunk_q >= ASYNC_MIN_TILES;
   return launch_pdl(lanczos_pass<S, R, TH, D, V, AY>, grid, NT, smem, s, p);
 }
@@ -268,7 +261,7 @@ __global__ void minmax_kernel(const double* v, long long n, double* out) {
 // ---------------------------------------------------------------------------
 // Engine: N independent problems sharing precision, stencil, boundary, m_max
 // ---------------------------------------------------------------------------
-enum { KIND_PASS = 0, KIND_RECOMBINE = 1, KIND_END = -1 };
+enum { KIND_PASS = 0, KIND_RECOMBINE = 1, KIND_STEP = 2, KIND_END = -1 };
 
 struct HostProblem {
   int nx = 0, ny = 0;
@@ -298,6 +291,11 @@ struct Engine {
   DevState* d_st = nullptr;        // nprob states
   DevState* h_st = nullptr;        // pinned mirror for read-back
   double* d_partials = nullptr;
+  // one-launch step (single problem): CTA partials by pass parity, barrier words
+  double* d_coop_slots = nullptr;
+  unsigned* d_coop_bar = nullptr;
+  int coop_cap = 0;                // CTAs the slot buffer holds
+  int step_mode = DIRAC_STEP_AUTO;
   int* d_blk_prob = nullptr;
   int* d_step = nullptr;
   // per-call tables: [Problem x nprob][ChebParams x nprob][FieldStep x nfield]
@@ -322,6 +320,11 @@ struct Engine {
   size_t ev_used = 0;
 
   int nprob() const { return (int)P.size(); }
+  bool use_step_kernel(int np) const {
+    if (np != 1 || !d_coop_slots) return false;
+    if (step_mode == DIRAC_STEP_AUTO) return precision == DIRAC_FP64;
+    return step_mode == DIRAC_STEP_ONE_LAUNCH;
+  }
   cudaError_t mark(int kind);
   dirac_status init(int n, const int* nx, const int* ny, const double* dx, const double* dy, double mass_,
                     double c_, int order_, int boundary_, int precision_, int m_max_, void* stream_);
@@ -425,6 +428,11 @@ dirac_status Engine::init(int n, const int* nx, const int* ny, const double* dx,
   CUDA_TRY(cudaMalloc(&d_st, sizeof(DevState) * n));
   CUDA_TRY(cudaMallocHost(&h_st, sizeof(DevState) * n));
   CUDA_TRY(cudaMalloc(&d_step, sizeof(int)));
+  if (n == 1) {
+    coop_cap = shape.n_sm * 8;     // the most resident CTAs of any pass kernel
+    CUDA_TRY(cudaMalloc(&d_coop_slots, 2 * 3 * sizeof(double) * coop_cap));
+    CUDA_TRY(cudaMalloc(&d_coop_bar, GRID_SYNC_WORDS * sizeof(unsigned)));
+  }
   CUDA_TRY(cudaMemsetAsync(d_st, 0, sizeof(DevState) * n, stream));
   CUDA_TRY(cudaEventCreateWithFlags(&tab_ev, cudaEventDisableTiming));
   // recombination blocks in proportion to the problem sizes
@@ -460,6 +468,8 @@ void Engine::release() {
   cudaFree(d_st);
   cudaFreeHost(h_st);
   cudaFree(d_partials);
+  cudaFree(d_coop_slots);
+  cudaFree(d_coop_bar);
   cudaFree(d_blk_prob);
   cudaFree(d_step);
   cudaFree(d_tab);
@@ -656,6 +666,22 @@ dirac_status Engine::run(vec4* const* psi, int nsteps, double dt, int m, double 
     lp.probe = 0;
     need_probe = false;
   }
+  if (use_step_kernel(np)) {
+    // one cooperative launch per step (the barrier words restart at zero)
+    CoopArgs ca;
+    ca.slots = d_coop_slots;
+    ca.bar = d_coop_bar;
+    ca.G = 0;
+    ca.cap = coop_cap;
+    for (int s = 0; s < nsteps; ++s) {
+      CUDA_TRY(cudaMemsetAsync(d_coop_bar, 0, GRID_SYNC_WORDS * sizeof(unsigned), stream));
+      CUDA_TRY(mark(KIND_STEP));
+      CUDA_TRY(launch_step(precision, th, order, diri, hasv, lp, shape.n_sm, ca, stream));
+      ++launches;
+    }
+    CUDA_TRY(mark(KIND_END));
+    return DIRAC_OK;
+  }
   // One step: m passes plus the spare launches for re-runs (every problem
   // runs its own next pass; launches with nothing left to do exit at once),
   // then the recombination.  The launches are the same at every step (the
@@ -748,7 +774,12 @@ dirac_status Engine::read_state(dirac_step_info* info) {
       }
     }
   }
-  if (bad) return fail(DIRAC_ENONFINITE, "non-finite value in a Lanczos reduction; psi left unchanged");
+  if (bad) {
+    for (int b = 0; b < np; ++b)
+      if (h_st[b].error == ERR_BARRIER)
+        return fail(DIRAC_ECUDA, "a grid barrier of the one-launch step timed out; psi left unchanged");
+    return fail(DIRAC_ENONFINITE, "non-finite value in a Lanczos reduction; psi left unchanged");
+  }
   return DIRAC_OK;
 }
 
@@ -1037,6 +1068,14 @@ dirac_status dirac_batch_use_graphs(dirac_batch* bt, int enable) {
 dirac_status dirac_use_graphs(dirac_ctx* ctx, int enable) {
   if (!ctx) return fail(DIRAC_EINVAL, "null context");
   ctx->e.use_graphs = enable != 0;
+  return DIRAC_OK;
+}
+
+dirac_status dirac_set_step_mode(dirac_ctx* ctx, int mode) {
+  if (!ctx) return fail(DIRAC_EINVAL, "null context");
+  if (mode != DIRAC_STEP_AUTO && mode != DIRAC_STEP_PASSES && mode != DIRAC_STEP_ONE_LAUNCH)
+    return fail(DIRAC_EINVAL, "unknown step mode %d", mode);
+  ctx->e.step_mode = mode;
   return DIRAC_OK;
 }
 

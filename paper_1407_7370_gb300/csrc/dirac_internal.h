@@ -34,6 +34,17 @@ struct CtxView {
 dirac_status ctx_view(dirac_ctx* ctx, CtxView* v);
 
 struct ChebParams;
+struct LaunchParams;
+struct CoopArgs;
+
+// FP32 passes stage their tiles by asynchronous copies from this many tiles
+// per CTA on (below that the extra barrier costs more than it hides)
+constexpr int ASYNC_MIN_TILES = 4;
+
+// One time step of the single problem in `p` as one cooperative launch
+// (lanczos_step); sets the grid, the chunks and ca.G.
+cudaError_t launch_step(int precision, int th, int order, bool diri, bool hasv, const LaunchParams& p, int n_sm,
+                        const CoopArgs& ca, cudaStream_t s);
 
 // [c0 - half, c0 + half] contains the spectrum of H - s for any vector
 // potential with |A_x| <= ax_max, |A_y| <= ay_max

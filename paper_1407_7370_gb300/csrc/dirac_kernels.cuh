@@ -193,6 +193,24 @@ __device__ __forceinline__ vec4 ldg4(const vec4* p) {
 }
 __device__ __forceinline__ float4 ldg4(const float4* p) { return __ldg(p); }
 
+// plain (coherent) loads for the one-launch step: its own earlier passes
+// wrote the data, so the read-only path may not serve it; the grid barrier's
+// acquire orders these loads after the other CTAs' stores
+__device__ __forceinline__ vec4 ldw4(const vec4* p) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+  const double2 a = q[0], b = q[1];
+  vec4 r;
+  r.x = a.x; r.y = a.y; r.z = b.x; r.w = b.y;
+  return r;
+}
+__device__ __forceinline__ float4 ldw4(const float4* p) { return *p; }
+
+template <bool COHERENT, class T>
+__device__ __forceinline__ T ld4(const T* p) {
+  if constexpr (COHERENT) return ldw4(p);
+  else return ldg4(p);
+}
+
 template <class S> struct Vec4;
 template <> struct Vec4<double> { using T = double4_32a; };
 template <> struct Vec4<float> { using T = float4; };
@@ -245,9 +263,8 @@ __device__ inline void cheb_expm_e1(const ChebParams& cp, int k, double alpha_j,
 // with plain loads up front; new values travel by shuffles.  rsqrt gives
 // sqrt(X), 1/X, sqrt(s2) and 1/sqrt(s2) with few dependent FP64 operations.
 // ---------------------------------------------------------------------------
-__device__ inline void finish_pass(const LaunchParams& lp, const Problem* pr, int i, double P, double Y,
-                                   double X) {
-  DevState* st = pr->st;
+__device__ inline void finish_pass(const LaunchParams& lp, const Problem* pr, DevState* st, int i, double P,
+                                   double Y, double X) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const double shift = pr->shift;
@@ -283,6 +300,7 @@ __device__ inline void finish_pass(const LaunchParams& lp, const Problem* pr, in
   const double psi_norm_old = st->psi_norm, cum_old = st->cum_err;
   const int redo_left = st->redo_left;
   const PassCoef pc_now = st->pc_cur;
+  __syncwarp();   // every lane has read the state before lane 0 updates it
 
   // scalar chain (every lane computes it; no broadcast needed)
   const double y = rsqrt(X);            // 1 / nu_i
@@ -415,10 +433,15 @@ __device__ __forceinline__ int cta_of_tile(int t, int q, int r) {
 template <class S, int R, int TH, int SUB>
 __host__ __device__ constexpr size_t dyn_smem_bytes() { return SUB == 1 ? 0 : SUB * tile_bytes<S, R, TH>(); }
 
-template <class S, int R, int TH, bool DIRI, bool HAS_V, bool HAS_AY>
-__global__ void __launch_bounds__(sub_workers<S>() * 32 * (TH / rows_per_thread<S, TH>()),
-                                  (min_blocks<S, TH, sub_workers<S>()>()))
-lanczos_pass(const __grid_constant__ LaunchParams lp) {
+// The body of one pass over this CTA's chunk.  COOP = false: a launch of
+// its own (lanczos_pass): per-problem tickets, the last CTA finishes.
+// COOP = true: inside the one-launch step (lanczos_step): one problem, the
+// state read from `coop_st`, coherent loads, and the CTA's partial sums
+// written to coop_slots[3 * blockIdx.x ...]; the caller synchronises the grid
+// and finishes.
+template <class S, int R, int TH, bool DIRI, bool HAS_V, bool HAS_AY, bool COOP>
+__device__ __forceinline__ void pass_body(const LaunchParams& lp, const DevState* coop_st, double* coop_slots,
+                                          int step) {
   using T4 = typename Vec4<S>::T;           // storage of y^ (and of q^ on the mixed path)
   constexpr int RPT = rows_per_thread<S, TH>();
   constexpr int SUB = sub_workers<S>();     // tile workers
@@ -430,9 +453,6 @@ lanczos_pass(const __grid_constant__ LaunchParams lp) {
   extern __shared__ __align__(32) unsigned char dyn_smem[];
   __shared__ double red[NW][3];
   __shared__ int last_flag;
-  // programmatic dependent launch: nothing the previous kernel wrote is read
-  // before this point
-  asm volatile("griddepcontrol.wait;" ::: "memory");
 
   const int cq = lp.chunk_q, cr = lp.chunk_r;
   const int t_begin = blockIdx.x * cq + min((int)blockIdx.x, cr);
@@ -441,7 +461,6 @@ lanczos_pass(const __grid_constant__ LaunchParams lp) {
   const int ltid = (int)threadIdx.x - sub * NTS;
   const int tx = ltid & 31, tg = ltid >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int step = *lp.step;
   constexpr bool F32 = sizeof(S) == sizeof(float);
   __shared__ __align__(32) S tile_s[SUB == 1 ? TH + 2 * R : 1][W][4];
   S(*const tile)[W][4] = SUB == 1 ? &tile_s[0]
@@ -470,7 +489,7 @@ lanczos_pass(const __grid_constant__ LaunchParams lp) {
   }
   for (int t = t_begin; t < t_end; ++b) {
     const Problem* pr = lp.probs + b;
-    const DevState* st = lp.states + b;
+    const DevState* st = COOP ? coop_st : lp.states + b;
     // independent loads first (all addresses are valid), then the branch
     const int stopped = st->stopped;
     const int i = lp.probe ? 1 : max(1, st->cur_pass);
@@ -510,16 +529,16 @@ lanczos_pass(const __grid_constant__ LaunchParams lp) {
         const size_t idx = (size_t)iy * nx + ix;
         if (q64) {
           const vec4* qsrc = (i == 1) ? pr->psi : static_cast<const vec4*>(q_prev);
-          cvt4(ldg4(qsrc + idx), qp);
+          cvt4(ld4<COOP>(qsrc + idx), qp);
         } else {
-          cvt4(ldg4(static_cast<const float4*>(q_prev) + idx), qp);
+          cvt4(ld4<COOP>(static_cast<const float4*>(q_prev) + idx), qp);
         }
         if (i == 1) {
 #pragma unroll
           for (int c = 0; c < 4; ++c) q[c] = qp[c];
         } else {
           S yv[4];
-          cvt4(ldg4(yprev + idx), yv);
+          cvt4(ld4<COOP>(yprev + idx), yv);
 #pragma unroll
           for (int c = 0; c < 4; ++c) q[c] = fma(-gdS, qp[c], gS * yv[c]);
         }
@@ -702,18 +721,25 @@ lanczos_pass(const __grid_constant__ LaunchParams lp) {
         s2 += __shfl_xor_sync(0xffffffffu, s2, o);
       }
       if (lane == 0) {
-        const int slot = blockIdx.x - cta_of_tile(pr->tile_begin, cq, cr);
-        pr->partials[3 * slot + 0] = s0;
-        pr->partials[3 * slot + 1] = s1;
-        pr->partials[3 * slot + 2] = s2;
-        // release our partial / acquire everybody else's
-        cuda::atomic_ref<unsigned, cuda::thread_scope_device> ticket(pr->st->counter);
-        last_flag = (ticket.fetch_add((unsigned)seg_tiles, cuda::memory_order_acq_rel) + seg_tiles ==
-                     (unsigned)pr->ntiles);
+        if constexpr (COOP) {
+          coop_slots[3 * blockIdx.x + 0] = s0;
+          coop_slots[3 * blockIdx.x + 1] = s1;
+          coop_slots[3 * blockIdx.x + 2] = s2;
+          last_flag = 0;
+        } else {
+          const int slot = blockIdx.x - cta_of_tile(pr->tile_begin, cq, cr);
+          pr->partials[3 * slot + 0] = s0;
+          pr->partials[3 * slot + 1] = s1;
+          pr->partials[3 * slot + 2] = s2;
+          // release our partial / acquire everybody else's
+          cuda::atomic_ref<unsigned, cuda::thread_scope_device> ticket(pr->st->counter);
+          last_flag = (ticket.fetch_add((unsigned)seg_tiles, cuda::memory_order_acq_rel) + seg_tiles ==
+                       (unsigned)pr->ntiles);
+        }
       }
     }
     __syncthreads();
-    if (last_flag) {
+    if (!COOP && last_flag) {
       // the problem is complete: the whole CTA sums its slots in a fixed
       // order (thread-strided, the warp tree, then the warps in turn), the
       // loads batched so that their L2 round trips overlap
@@ -745,11 +771,21 @@ lanczos_pass(const __grid_constant__ LaunchParams lp) {
 #pragma unroll
         for (int w = 1; w < NW; ++w) { t0 += red[w][0]; t1 += red[w][1]; t2 += red[w][2]; }
         if (lane == 0) pr->st->counter = 0u;
-        finish_pass(lp, pr, i, t0, t1, t2);
+        finish_pass(lp, pr, pr->st, i, t0, t1, t2);
       }
     }
     __syncthreads();
   }
+}
+
+template <class S, int R, int TH, bool DIRI, bool HAS_V, bool HAS_AY>
+__global__ void __launch_bounds__(sub_workers<S>() * 32 * (TH / rows_per_thread<S, TH>()),
+                                  (min_blocks<S, TH, sub_workers<S>()>()))
+lanczos_pass(const __grid_constant__ LaunchParams lp) {
+  // programmatic dependent launch: nothing the previous kernel wrote is read
+  // before this point
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  pass_body<S, R, TH, DIRI, HAS_V, HAS_AY, false>(lp, nullptr, nullptr, *lp.step);
   // the next kernel may be scheduled now (it waits for our completion)
   asm volatile("griddepcontrol.launch_dependents;");
 }
@@ -761,6 +797,50 @@ lanczos_pass(const __grid_constant__ LaunchParams lp) {
 // enters the (small) Krylov corrections.
 // Blocks are dealt to problems in proportion to their size.
 // ---------------------------------------------------------------------------
+template <bool MIXED>
+__device__ __forceinline__ void recombine_site(vec4* psi, const void* basis_v, long long n, long long s, int k,
+                                               const double* cr, const double* ci, const float* fr,
+                                               const float* fi) {
+  if constexpr (!MIXED) {
+    const vec4* basis = static_cast<const vec4*>(basis_v);
+    const vec4 q = psi[s];
+    double ur = cr[1] * q.x - ci[1] * q.y, ui = cr[1] * q.y + ci[1] * q.x;
+    double dr = cr[1] * q.z - ci[1] * q.w, di = cr[1] * q.w + ci[1] * q.z;
+    for (int j = 2; j <= k; ++j) {
+      const vec4* vp = basis + (size_t)(j - 2) * n + s;
+      const vec4 v = *vp;
+      const double a = cr[j], bb = ci[j];
+      ur = fma(a, v.x, fma(-bb, v.y, ur));
+      ui = fma(a, v.y, fma(bb, v.x, ui));
+      dr = fma(a, v.z, fma(-bb, v.w, dr));
+      di = fma(a, v.w, fma(bb, v.z, di));
+    }
+    vec4 o;
+    o.x = ur; o.y = ui; o.z = dr; o.w = di;
+    psi[s] = o;
+  } else {
+    const float4* basis = static_cast<const float4*>(basis_v);
+    const double ar = cr[1], ai = ci[1];
+    float ur = 0.f, ui = 0.f, dr = 0.f, di = 0.f;
+    for (int j = 2; j <= k; ++j) {
+      const float4* vp = basis + (size_t)(j - 2) * n + s;
+      const float4 v = *vp;
+      const float a = fr[j], bb = fi[j];
+      ur = fmaf(a, v.x, fmaf(-bb, v.y, ur));
+      ui = fmaf(a, v.y, fmaf(bb, v.x, ui));
+      dr = fmaf(a, v.z, fmaf(-bb, v.w, dr));
+      di = fmaf(a, v.w, fmaf(bb, v.z, di));
+    }
+    const vec4 q = psi[s];
+    vec4 o;
+    o.x = fma(ar, q.x, fma(-ai, q.y, (double)ur));
+    o.y = fma(ar, q.y, fma(ai, q.x, (double)ui));
+    o.z = fma(ar, q.z, fma(-ai, q.w, (double)dr));
+    o.w = fma(ar, q.w, fma(ai, q.z, (double)di));
+    psi[s] = o;
+  }
+}
+
 template <bool MIXED>
 __global__ void __launch_bounds__(256) recombine(const __grid_constant__ RecombParams rp) {
   asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -790,47 +870,157 @@ __global__ void __launch_bounds__(256) recombine(const __grid_constant__ RecombP
   const long long n = (long long)pr->nx * pr->ny;
   const long long stride = (long long)pr->rblk_count * blockDim.x;
   vec4* psi = const_cast<vec4*>(pr->psi);
-  if constexpr (!MIXED) {
-    const vec4* basis = static_cast<const vec4*>(pr->basis);
-    for (long long s = (long long)lb * blockDim.x + threadIdx.x; s < n; s += stride) {
-      const vec4 q = psi[s];
-      double ur = cr[1] * q.x - ci[1] * q.y, ui = cr[1] * q.y + ci[1] * q.x;
-      double dr = cr[1] * q.z - ci[1] * q.w, di = cr[1] * q.w + ci[1] * q.z;
-      for (int j = 2; j <= k; ++j) {
-        const vec4 v = basis[(size_t)(j - 2) * n + s];
-        const double a = cr[j], bb = ci[j];
-        ur = fma(a, v.x, fma(-bb, v.y, ur));
-        ui = fma(a, v.y, fma(bb, v.x, ui));
-        dr = fma(a, v.z, fma(-bb, v.w, dr));
-        di = fma(a, v.w, fma(bb, v.z, di));
+  for (long long s = (long long)lb * blockDim.x + threadIdx.x; s < n; s += stride)
+    recombine_site<MIXED>(psi, pr->basis, n, s, k, cr, ci, fr, fi);
+  asm volatile("griddepcontrol.launch_dependents;");
+}
+
+// ---------------------------------------------------------------------------
+// One time step of one problem in one cooperative launch (every CTA
+// resident): the passes separated by grid-wide barriers instead of kernel
+// boundaries, then the recombination.  After each pass every CTA sums all
+// CTA partials in the same fixed order and runs the scalar update on its own
+// shared-memory copy of the state, so that all copies stay identical
+// (bitwise: same inputs, same operations) and no second barrier is needed.
+// Partials are double-buffered by pass parity: a CTA can run at most one
+// pass ahead of the slowest one, which is still reading the other buffer.
+// ---------------------------------------------------------------------------
+constexpr int ERR_BARRIER = 8;                    // a grid barrier timed out
+constexpr unsigned GRID_SYNC_SPIN_MAX = 1u << 22; // polls (with ~100 ns naps) before giving up
+constexpr int GRID_SYNC_WORDS = 4;                // arrivals, generation, timeout flag, spare
+
+struct CoopArgs {
+  double* slots;   // 2 x 3 x cap doubles: CTA partials (P, Y, X) by pass parity
+  unsigned* bar;   // GRID_SYNC_WORDS words, zeroed before each launch
+  int G;           // CTAs of the launch
+  int cap;         // CTAs the slot buffer holds
+};
+
+// Barrier of all CTAs of a cooperative launch.  Thread 0 of each CTA arrives
+// (release of the CTA's writes, ordered by the __syncthreads before it) and
+// waits for the generation to advance (acquire).  False after a timeout
+// (bar[2] set), after which every waiting CTA gives up as well.  One counter
+// and one polled word serve the one-CTA-per-SM launches of the FP64 path
+// well; with many CTAs per SM their contention outweighs what the launch
+// boundaries cost, which is why the FP32 path keeps per-pass launches.
+__device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned G) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    cuda::atomic_ref<unsigned, cuda::thread_scope_device> arrived(bar[0]), gen(bar[1]), timeout(bar[2]);
+    const unsigned g0 = gen.load(cuda::memory_order_acquire);
+    int ok = 1;
+    __threadfence();
+    if (arrived.fetch_add(1u, cuda::memory_order_acq_rel) == G - 1u) {
+      arrived.store(0u, cuda::memory_order_relaxed);
+      gen.store(g0 + 1u, cuda::memory_order_release);
+    } else {
+      unsigned spins = 0;
+      while (gen.load(cuda::memory_order_acquire) == g0) {
+        if (timeout.load(cuda::memory_order_relaxed) != 0u || ++spins > GRID_SYNC_SPIN_MAX) {
+          timeout.store(1u, cuda::memory_order_relaxed);
+          ok = 0;
+          break;
+        }
+        __nanosleep(100);
       }
-      vec4 o;
-      o.x = ur; o.y = ui; o.z = dr; o.w = di;
-      psi[s] = o;
     }
-  } else {
-    const float4* basis = static_cast<const float4*>(pr->basis);
-    const double ar = cr[1], ai = ci[1];
-    for (long long s = (long long)lb * blockDim.x + threadIdx.x; s < n; s += stride) {
-      float ur = 0.f, ui = 0.f, dr = 0.f, di = 0.f;
-      for (int j = 2; j <= k; ++j) {
-        const float4 v = basis[(size_t)(j - 2) * n + s];
-        const float a = fr[j], bb = fi[j];
-        ur = fmaf(a, v.x, fmaf(-bb, v.y, ur));
-        ui = fmaf(a, v.y, fmaf(bb, v.x, ui));
-        dr = fmaf(a, v.z, fmaf(-bb, v.w, dr));
-        di = fmaf(a, v.w, fmaf(bb, v.z, di));
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+template <class S, int R, int TH, bool DIRI, bool HAS_V, bool HAS_AY>
+__global__ void __launch_bounds__(sub_workers<S>() * 32 * (TH / rows_per_thread<S, TH>()),
+                                  (min_blocks<S, TH, sub_workers<S>()>()))
+lanczos_step(const __grid_constant__ LaunchParams lp, const __grid_constant__ CoopArgs ca) {
+  constexpr bool F32 = sizeof(S) == sizeof(float);
+  constexpr int NT = sub_workers<S>() * 32 * (TH / rows_per_thread<S, TH>());
+  __shared__ DevState sst;
+  __shared__ double cr_s[KMAX + 2], ci_s[KMAX + 2];
+  __shared__ float fr_s[KMAX + 2], fi_s[KMAX + 2];
+  const Problem* pr = lp.probs;
+  DevState* gst = lp.states;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  {
+    const unsigned* src = reinterpret_cast<const unsigned*>(gst);
+    unsigned* dst = reinterpret_cast<unsigned*>(&sst);
+    for (int w = threadIdx.x; w < (int)(sizeof(DevState) / sizeof(unsigned)); w += NT) dst[w] = __ldcg(src + w);
+  }
+  const int step = __ldcg(lp.step);
+  __syncthreads();
+  const int max_iter = lp.m + lp.redo_budget;
+  int iter = 0;
+  while (!sst.stopped && iter < max_iter) {
+    const int i = max(1, sst.cur_pass);
+    double* slots = ca.slots + (iter & 1) * 3 * ca.G;
+    pass_body<S, R, TH, DIRI, HAS_V, HAS_AY, true>(lp, &sst, slots, step);
+    ++iter;
+    if (!grid_sync(ca.bar, (unsigned)ca.G)) {
+      if (threadIdx.x == 0) { gst->error = ERR_BARRIER; gst->stopped = 1; }
+      return;   // psi untouched; the host reports the timeout
+    }
+    if (warp == 0) {   // the grid totals, in the same order in every CTA
+      constexpr int SB = 4;   // loads in flight per lane
+      double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+      for (int c0 = lane; c0 < ca.G; c0 += SB * 32) {
+        double v[SB][3];
+#pragma unroll
+        for (int k = 0; k < SB; ++k) {
+          const int c = c0 + k * 32;
+          const double* ps = slots + 3 * (c < ca.G ? c : 0);
+          v[k][0] = c < ca.G ? __ldcg(ps) : 0.0;
+          v[k][1] = c < ca.G ? __ldcg(ps + 1) : 0.0;
+          v[k][2] = c < ca.G ? __ldcg(ps + 2) : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < SB; ++k) { t0 += v[k][0]; t1 += v[k][1]; t2 += v[k][2]; }
       }
-      const vec4 q = psi[s];
-      vec4 o;
-      o.x = fma(ar, q.x, fma(-ai, q.y, (double)ur));
-      o.y = fma(ar, q.y, fma(ai, q.x, (double)ui));
-      o.z = fma(ar, q.z, fma(-ai, q.w, (double)dr));
-      o.w = fma(ar, q.w, fma(ai, q.z, (double)di));
-      psi[s] = o;
+      t0 = warp_sum(t0);
+      t1 = warp_sum(t1);
+      t2 = warp_sum(t2);
+      finish_pass(lp, pr, &sst, i, t0, t1, t2);
+    }
+    __syncthreads();
+  }
+  const int err = sst.error;
+  if (!err) {
+    // psi <- sum_j C_j q^_j on this CTA's tiles (no CTA reads psi any more)
+    if (threadIdx.x <= KMAX) {
+      cr_s[threadIdx.x] = sst.coef_re[threadIdx.x];
+      ci_s[threadIdx.x] = sst.coef_im[threadIdx.x];
+      fr_s[threadIdx.x] = (float)cr_s[threadIdx.x];
+      fi_s[threadIdx.x] = (float)ci_s[threadIdx.x];
+    }
+    __syncthreads();
+    const int cq = lp.chunk_q, cr = lp.chunk_r;
+    const int t_begin = blockIdx.x * cq + min((int)blockIdx.x, cr);
+    const int t_end = t_begin + cq + ((int)blockIdx.x < cr ? 1 : 0);
+    const long long n = (long long)pr->nx * pr->ny;
+    const int k = sst.k_used;
+    vec4* psi = const_cast<vec4*>(pr->psi);
+    for (int tt = t_begin; tt < t_end; ++tt) {
+      const int x0 = (tt % pr->tiles_x) * TILE_W, y0 = (tt / pr->tiles_x) * TH;
+      for (int e = threadIdx.x; e < TILE_W * TH; e += NT) {
+        const int x = x0 + (e & (TILE_W - 1)), y = y0 + e / TILE_W;
+        if (x < pr->nx && y < pr->ny)
+          recombine_site<F32>(psi, pr->basis, n, (long long)y * pr->nx + x, k, cr_s, ci_s, fr_s, fi_s);
+      }
     }
   }
-  asm volatile("griddepcontrol.launch_dependents;");
+  if (blockIdx.x == 0) {   // publish the state (identical in every CTA), re-armed for the next step
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (!err) { sst.stopped = 0; sst.cur_pass = 1; sst.redo_left = lp.redo_budget; }
+      *const_cast<int*>(lp.step) = step + 1;
+    }
+    __syncthreads();
+    const unsigned* src = reinterpret_cast<const unsigned*>(&sst);
+    unsigned* dst = reinterpret_cast<unsigned*>(gst);
+    for (int w = threadIdx.x; w < (int)(sizeof(DevState) / sizeof(unsigned)); w += NT) dst[w] = src[w];
+  }
 }
 
 // ---------------------------------------------------------------------------

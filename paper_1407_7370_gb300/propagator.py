@@ -236,16 +236,22 @@ class Propagator:
     def use_graphs(self, enable: bool = True):
         nat.check(nat.lib().dirac_use_graphs(self._ctx, 1 if enable else 0))
 
+    def set_step_mode(self, mode: str = "auto"):
+        """'auto', 'passes' or 'one_launch' (see dirac_set_step_mode)."""
+        code = {"auto": nat.STEP_AUTO, "passes": nat.STEP_PASSES, "one_launch": nat.STEP_ONE_LAUNCH}[mode]
+        nat.check(nat.lib().dirac_set_step_mode(self._ctx, code))
+
     def profile(self, enable: bool = True):
         """Start/stop per-kernel CUDA-event timing (see dirac_profile_enable)."""
         nat.check(nat.lib().dirac_profile_enable(self._ctx, 1 if enable else 0))
 
     def profile_read(self) -> dict:
-        """{kind: (total ms, launches)} since the previous read; kinds 'pass', 'recombine'."""
+        """{kind: (total ms, launches)} since the previous read; kinds 'pass',
+        'recombine' and 'step' (the one-launch step, see set_step_mode)."""
         ms = (ctypes.c_double * nat.KERNEL_KINDS)()
         n = (ctypes.c_longlong * nat.KERNEL_KINDS)()
         nat.check(nat.lib().dirac_profile_read(self._ctx, ms, n))
-        return {"pass": (ms[0], n[0]), "recombine": (ms[1], n[1])}
+        return {"pass": (ms[0], n[0]), "recombine": (ms[1], n[1]), "step": (ms[2], n[2])}
 
     @property
     def kernel_launches(self) -> int:

@@ -35,10 +35,11 @@ def built():
 
 
 def gpu_run(grid, psi0, dt, m, steps, V=None, A=(0.0, 0.0), order=2, boundary="periodic",
-            shift=0.0, tol=0.0, A_steps=None, info=True, precision="fp64"):
+            shift=0.0, tol=0.0, A_steps=None, info=True, precision="fp64", step_mode="auto"):
     from paper_1407_7370_gb300 import Propagator
     prop = Propagator(grid.nx, grid.ny, grid.dx, grid.dy, order=order, boundary=boundary, m_max=m,
                       precision=precision)
+    prop.set_step_mode(step_mode)
     prop.set_fields(None if V is None else torch.from_numpy(V).cuda(), A=A, shift=shift)
     psi = torch.from_numpy(np.ascontiguousarray(psi0)).cuda()
     inf = prop.steps(psi, steps, dt, m, tol=tol, A=A_steps, info=info)
@@ -230,11 +231,50 @@ def test_host_buffer_call_equals_device_call():
     assert np.array_equal(host.numpy(), dev)
 
 
-def test_kernel_launch_count():
+@pytest.mark.parametrize("precision,mode,per_step", [
+    ("fp64", "passes", 7 + 2 + 1),      # m passes + 2 spare launches for re-runs + recombine
+    ("fp64", "one_launch", 1),
+    ("fp64", "auto", 1),
+    ("mixed", "auto", 7 + 3 + 1),       # the mixed path keeps 2 + m / 5 spare launches
+    ("mixed", "one_launch", 1)])
+def test_kernel_launch_count(precision, mode, per_step):
     g = wl.Grid(32, 32, 0.1, 0.1)
-    _, _, prop = gpu_run(g, wl.positive_energy_packet(g), 1e-4, 7, 3)
-    # probe + (m passes + 2 spare launches for re-runs + recombine) per step
-    assert prop.kernel_launches == 1 + 3 * (7 + 2 + 1)
+    _, _, prop = gpu_run(g, wl.positive_energy_packet(g), 1e-4, 7, 3, precision=precision,
+                         step_mode=mode)
+    assert prop.kernel_launches == 1 + 3 * per_step     # the probe, then the steps
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("nx,ny,order,boundary,hasv,tol", [(45, 37, 2, "periodic", True, 0.0),
+                                                           (70, 33, 4, "dirichlet", False, 0.0),
+                                                           (96, 64, 2, "periodic", False, 1e-9)])
+def test_one_launch_step_agrees_with_per_pass_launches(precision, nx, ny, order, boundary, hasv, tol):
+    """The cooperative one-launch step and the per-pass launches compute the
+    same recurrence; only the order in which CTA partials are added differs."""
+    g = wl.Grid(nx, ny, 0.1, 0.1)
+    psi0 = wl.positive_energy_packet(g, p0=(3.0, -2.0)) + 0.05 * wl.random_spinor(g, 9)
+    V = wl.soft_core(g, 1.0) if hasv else None
+    rng = np.random.default_rng(3)
+    A = rng.uniform(-5, 5, size=(6, 2))
+    shift = 137.036 ** 2 if precision == "mixed" else 0.0
+    outs = {}
+    for mode in ("passes", "one_launch"):
+        psi, inf, _ = gpu_run(g, psi0, 1e-4, 12, 6, V=V, order=order, boundary=boundary, tol=tol,
+                              A_steps=A, precision=precision, step_mode=mode, shift=shift)
+        outs[mode] = (psi, inf)
+    a, ia = outs["passes"]
+    b, ib = outs["one_launch"]
+    assert ia.k_used == ib.k_used
+    assert lz.rel_l2(b, a) <= (1e-13 if precision == "fp64" else 1e-6)
+    op = oracle_op(g, V=V, order=order, boundary=ham.DIRICHLET if boundary == "dirichlet" else ham.PERIODIC,
+                   shift=shift)
+    ref = psi0.copy()
+    for s in range(6):
+        op.A = tuple(A[s])
+        ref, _ = lz.krylov_step(op, ref, 1e-4, 12, tol=tol)
+    tol_ref = fp64_tol(6, 1e-4) if precision == "fp64" else \
+        mixed_tol(6, 1e-4, max(hnorm(g, tuple(a), V, order) for a in A))
+    assert lz.rel_l2(b, ref) <= tol_ref
 
 
 @pytest.mark.slow

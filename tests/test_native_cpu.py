@@ -64,7 +64,19 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(lib):
         assert not ctx.value
 
 
+def test_binding_constants_match_the_header():
+    import re
+    text = open(nat.HEADER).read()
+    defs = dict(re.findall(r"#define\s+(DIRAC_\w+)\s+(-?\d+)", text))
+    for name, value in (("DIRAC_KERNEL_KINDS", nat.KERNEL_KINDS), ("DIRAC_STEP_AUTO", nat.STEP_AUTO),
+                        ("DIRAC_STEP_PASSES", nat.STEP_PASSES),
+                        ("DIRAC_STEP_ONE_LAUNCH", nat.STEP_ONE_LAUNCH),
+                        ("DIRAC_EIG_RITZ_MAX", nat.EIG_RITZ_MAX), ("DIRAC_EIG_ITER_MAX", nat.EIG_ITER_MAX)):
+        assert int(defs[name]) == value, name
+
+
 def test_calls_on_null_context_fail_cleanly(lib):
+    assert lib.dirac_set_step_mode(None, 0) == nat.EINVAL
     assert lib.dirac_set_fields(None, None, 0.0, 0.0, 0.0) == nat.EINVAL
     assert lib.dirac_lanczos_step(None, None, 1e-4, 10, 0.0, None) == nat.EINVAL
     assert lib.dirac_sync(None) == nat.EINVAL
