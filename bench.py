@@ -40,10 +40,22 @@ SITE_BYTES = 32            # complex128 spinor
 PASS_BYTES_PER_SITE = 3 * SITE_BYTES   # read q_i, read q_{i-1}, write q_{i+1} (V = 0)
 PASS_BYTES_PER_SITE_MIXED = 3 * 16      # the same accesses in complex64
 PASS_FLOPS_PER_SITE = 80   # FP64 flops of one Lanczos iteration per site
+RECOMB_FLOPS_PER_VECTOR = 16   # psi += C_j q_j: a complex multiply-add on both spinor components
 
-# DRAM traffic per launch from the last ncu capture of the pass kernel, valid
-# only for the kernel source it was taken with (sha1 of dirac_kernels.cuh).
-TRAFFIC = {"fp64": ("69d9e39dafda", 69.59e6 + 20.07e6), "mixed": ("69d9e39dafda", 33.63e6 + 0.65e6)}
+
+def STEP_BYTES_PER_SITE(m):          # algorithmic bytes of one step: (4m - 1) site-vectors
+    return (4 * m - 1) * SITE_BYTES
+
+
+def STEP_BYTES_PER_SITE_MIXED(m):    # complex64 basis; psi read and written in complex128
+    return (4 * m - 3) * 16 + 2 * SITE_BYTES
+
+
+# DRAM traffic per launch from the last ncu capture of each kernel on the
+# configured grid, valid only for the kernel source it was taken with (sha1 of
+# dirac_kernels.cuh).
+TRAFFIC = {"lanczos_step<double>": ("23d3d1b180ed", 1.637626e9 + 1.302642e9),
+           "lanczos_pass<float>": ("23d3d1b180ed", 33.634816e6 + 0.617728e6)}
 
 
 def kernel_sha() -> str:
@@ -52,8 +64,8 @@ def kernel_sha() -> str:
     return hashlib.sha1(open(path, "rb").read()).hexdigest()[:12]
 
 
-def traffic_for(prec: str, grid):
-    rec = TRAFFIC.get(prec)
+def traffic_for(kernel: str, grid):
+    rec = TRAFFIC.get(kernel)
     if grid.n_sites != CFG["grid"].n_sites:   # captured on the configured grid only
         return None
     if rec and rec[0] == kernel_sha():
@@ -562,11 +574,20 @@ def run_ours(args):
         return world * g.n_sites * m * steps / t
 
     def kernel_stats(r):
-        # per algorithmic pass: the pass-kernel time of a step over m (the
-        # spare launches kept for re-runs carry no data and are included)
+        """The dominant kernel of a run: the one-launch step (all passes and
+        the recombination of a step per launch) or, with per-pass launches,
+        the pass kernel, timed per algorithmic pass (the pass-kernel time of
+        a step over m; the spare launches kept for re-runs carry no data and
+        are included)."""
         pass_ms, pass_n = r["prof"]["pass"]
         rec_ms, rec_n = r["prof"]["recombine"]
-        return (pass_ms / K / m / 1e3, pass_ms / (pass_ms + rec_ms), rec_ms / max(1, rec_n) / 1e3)
+        step_ms, step_n = r["prof"].get("step", (0.0, 0))
+        total = pass_ms + rec_ms + step_ms
+        if step_n:
+            return {"one_launch": True, "launch_s": step_ms / step_n / 1e3, "share": step_ms / total,
+                    "rec_s": None}
+        return {"one_launch": False, "launch_s": pass_ms / K / m / 1e3, "share": pass_ms / total,
+                "rec_s": rec_ms / max(1, rec_n) / 1e3}
 
     if args.only:
         r = runs[args.only]
@@ -577,36 +598,47 @@ def run_ours(args):
     bytes_step = g.n_sites * SITE_BYTES
     # FP64 path: bound by the FP64 pipe
     f = runs["fp64"]
-    f_pass, f_share, f_rec = kernel_stats(f)
+    fk = kernel_stats(f)
     fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12   # TFLOP/s, see the design doc
-    flops = PASS_FLOPS_PER_SITE * g.n_sites / f_pass / 1e12
+    if fk["one_launch"]:
+        f_kernel = "lanczos_step<double>"
+        f_flops_site = (PASS_FLOPS_PER_SITE + RECOMB_FLOPS_PER_VECTOR) * m   # one launch = one step
+        f_bytes_site = STEP_BYTES_PER_SITE(m)
+    else:
+        f_kernel = "lanczos_pass<double>"
+        f_flops_site, f_bytes_site = PASS_FLOPS_PER_SITE, PASS_BYTES_PER_SITE
+    flops = f_flops_site * g.n_sites / fk["launch_s"] / 1e12
     roofline = {"bound": "alu", "achieved": flops, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": flops / fp64_peak, "traffic": traffic_for("fp64", g),
-                "kernel": "lanczos_pass<double>", "kernel_avg_us": f_pass * 1e6,
-                "kernel_share": f_share,
+                "frac": flops / fp64_peak, "traffic": traffic_for(f_kernel, g),
+                "kernel": f_kernel, "kernel_avg_us": fk["launch_s"] * 1e6,
+                "kernel_share": fk["share"], "flops_per_site_per_launch": f_flops_site,
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz "
                                "(probe measured 1.19 TFLOP/s)"}
-    f_gbs = PASS_BYTES_PER_SITE * g.n_sites / f_pass / 1e9
+    f_gbs = f_bytes_site * g.n_sites / fk["launch_s"] / 1e9
     # mixed path: bound by HBM
     x = runs["mixed"]
-    x_pass, x_share, x_rec = kernel_stats(x)
-    x_gbs = PASS_BYTES_PER_SITE_MIXED * g.n_sites / x_pass / 1e9
+    xk = kernel_stats(x)
+    if xk["one_launch"]:
+        x_kernel, x_bytes_site = "lanczos_step<float>", STEP_BYTES_PER_SITE_MIXED(m)
+    else:
+        x_kernel, x_bytes_site = "lanczos_pass<float>", PASS_BYTES_PER_SITE_MIXED
+    x_gbs = x_bytes_site * g.n_sites / xk["launch_s"] / 1e9
     err = float(torch.linalg.vector_norm(x["result"] - f["result"]) /
                 torch.linalg.vector_norm(f["result"]))
     mixed = {"value": site_rate(x["t"], K), "unit": UNIT, "ms_per_step": 1e3 * x["t"] / K,
              "dtype": "f32 stencil/basis + f64 scalars and state",
              "roofline": {"bound": "hbm", "achieved": x_gbs, "peak": hbm_peak, "unit": "GB/s",
-                          "frac": x_gbs / hbm_peak, "traffic": traffic_for("mixed", g),
-                          "kernel": "lanczos_pass<float>", "kernel_avg_us": x_pass * 1e6,
-                          "kernel_share": x_share, "peak_source": hbm_src,
-                          "bytes_per_site": PASS_BYTES_PER_SITE_MIXED},
+                          "frac": x_gbs / hbm_peak, "traffic": traffic_for(x_kernel, g),
+                          "kernel": x_kernel, "kernel_avg_us": xk["launch_s"] * 1e6,
+                          "kernel_share": xk["share"], "peak_source": hbm_src,
+                          "bytes_per_site": x_bytes_site},
              "error_vs_fp64": {"rel_l2": err, "per_unit_time": err / (K * dt),
                                "steps": K, "simulated_time": K * dt},
              "e2e": {"value": site_rate(x["te"], x["Ke"]), "unit": UNIT,
                      "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": bytes_step,
                      "steps": x["Ke"]},
              "gpu_launches": x["launches"], "clocks": x["clocks"],
-             "recombine_avg_us": x_rec * 1e6,
+             "recombine_avg_us": None if xk["rec_s"] is None else xk["rec_s"] * 1e6,
              "speedup_vs_fp64": f["t"] / x["t"]}
     line = None
     if rank == 0:
@@ -622,7 +654,7 @@ def run_ours(args):
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roofline,
                 "hbm": {"achieved": f_gbs, "peak": hbm_peak, "unit": "GB/s",
-                        "frac": f_gbs / hbm_peak, "bytes_per_site": PASS_BYTES_PER_SITE,
+                        "frac": f_gbs / hbm_peak, "bytes_per_site": f_bytes_site,
                         "peak_source": hbm_src},
                 "e2e": {"value": site_rate(f["te"], f["Ke"]), "unit": UNIT,
                         "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": bytes_step,
@@ -638,7 +670,7 @@ def run_ours(args):
                 "mixed": mixed,
                 "diagnostics": {"k_used": f["info"].k_used, "err_est_last": f["info"].err_est,
                                 "cum_err_est": f["info"].cum_err, "energy": f["info"].energy,
-                                "recombine_avg_us": f_rec * 1e6}}
+                                "recombine_avg_us": None if fk["rec_s"] is None else fk["rec_s"] * 1e6}}
         if not args.no_batch:
             line["batched"] = measure_batch(args, torch, world, dist, local, pk)
             line["batched"]["speedup_mixed_batched_vs_fp64_single"] = \

@@ -3,7 +3,9 @@
 // One time step (Sec. 4, Eq. 17) is m launches of `lanczos_pass` (one Lanczos
 // iteration each, Fig. 1 / Eq. 4) and one launch of `recombine`.  Every launch
 // covers a table of independent problems (grids of any size); a single
-// propagation is a table of one.
+// propagation is a table of one.  For a single problem the same pass body can
+// instead run inside `lanczos_step`, one cooperative launch per time step
+// whose passes are separated by grid-wide barriers (see there).
 //
 // Pass i (1-based) works on unnormalised vectors whose scales are tracked by
 // device scalars:
