@@ -274,6 +274,16 @@ dirac_status dirac_use_graphs(dirac_ctx* ctx, int enable);
 #define DIRAC_STEP_ONE_LAUNCH 2
 dirac_status dirac_set_step_mode(dirac_ctx* ctx, int mode);
 
+/*
+ * Test of the failure path of the one-launch step: runs one step whose grid
+ * barriers wait for one CTA more than the launch has, so that every bounded
+ * wait runs out (about a second); no fault, no hang.  Returns the status the
+ * context reports afterwards -- DIRAC_ECUDA, psi_dev (complex128 [ny][nx][2],
+ * device) untouched -- and leaves the context usable.  DIRAC_ESTATE on a
+ * context without the one-launch step (fields not set: DIRAC_ESTATE too).
+ */
+dirac_status dirac_debug_barrier_timeout(dirac_ctx* ctx, void* psi_dev, double dt, int m);
+
 /* dirac_profile_enable / dirac_profile_read / dirac_kernel_launches for a batch. */
 dirac_status dirac_batch_profile_enable(dirac_batch* batch, int enable);
 dirac_status dirac_batch_profile_read(dirac_batch* batch, double* ms, long long* launches);

@@ -296,6 +296,7 @@ struct Engine {
   unsigned* d_coop_bar = nullptr;
   int coop_cap = 0;                // CTAs the slot buffer holds
   int step_mode = DIRAC_STEP_AUTO;
+  int barrier_extra = 0;           // 1 only inside dirac_debug_barrier_timeout
   int* d_blk_prob = nullptr;
   int* d_step = nullptr;
   // per-call tables: [Problem x nprob][ChebParams x nprob][FieldStep x nfield]
@@ -673,6 +674,7 @@ dirac_status Engine::run(vec4* const* psi, int nsteps, double dt, int m, double 
     ca.bar = d_coop_bar;
     ca.G = 0;
     ca.cap = coop_cap;
+    ca.bar_count = barrier_extra;
     for (int s = 0; s < nsteps; ++s) {
       CUDA_TRY(cudaMemsetAsync(d_coop_bar, 0, GRID_SYNC_WORDS * sizeof(unsigned), stream));
       CUDA_TRY(mark(KIND_STEP));
@@ -1069,6 +1071,22 @@ dirac_status dirac_use_graphs(dirac_ctx* ctx, int enable) {
   if (!ctx) return fail(DIRAC_EINVAL, "null context");
   ctx->e.use_graphs = enable != 0;
   return DIRAC_OK;
+}
+
+dirac_status dirac_debug_barrier_timeout(dirac_ctx* ctx, void* psi_dev, double dt, int m) {
+  if (!ctx) return fail(DIRAC_EINVAL, "null context");
+  if (!psi_dev) return fail(DIRAC_EINVAL, "null psi");
+  Engine& e = ctx->e;
+  if (!e.d_coop_slots) return fail(DIRAC_ESTATE, "no one-launch step on this context");
+  const int mode = e.step_mode;
+  e.step_mode = DIRAC_STEP_ONE_LAUNCH;
+  e.barrier_extra = 1;
+  vec4* psi = static_cast<vec4*>(psi_dev);
+  dirac_status s = e.run(&psi, 1, dt, m, 0.0, nullptr);
+  e.barrier_extra = 0;
+  e.step_mode = mode;
+  if (s != DIRAC_OK) return s;
+  return e.read_state(nullptr);
 }
 
 dirac_status dirac_set_step_mode(dirac_ctx* ctx, int mode) {

@@ -42,7 +42,9 @@ struct CoopArgs;
 constexpr int ASYNC_MIN_TILES = 4;
 
 // One time step of the single problem in `p` as one cooperative launch
-// (lanczos_step); sets the grid, the chunks and ca.G.
+// (lanczos_step); sets the grid, the chunks and ca.G.  ca.bar_count on entry:
+// arrivals the barriers wait for beyond the launch's CTAs (0; 1 only in the
+// test of the barrier timeout).
 cudaError_t launch_step(int precision, int th, int order, bool diri, bool hasv, const LaunchParams& p, int n_sm,
                         const CoopArgs& ca, cudaStream_t s);
 

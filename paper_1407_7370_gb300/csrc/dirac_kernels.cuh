@@ -888,7 +888,7 @@ __global__ void __launch_bounds__(256) recombine(const __grid_constant__ RecombP
 // pass ahead of the slowest one, which is still reading the other buffer.
 // ---------------------------------------------------------------------------
 constexpr int ERR_BARRIER = 8;                    // a grid barrier timed out
-constexpr unsigned GRID_SYNC_SPIN_MAX = 1u << 22; // polls (with ~100 ns naps) before giving up
+constexpr unsigned GRID_SYNC_SPIN_MAX = 1u << 20; // polls (~100 ns nap + an L2 round trip each: about a second)
 constexpr int GRID_SYNC_WORDS = 4;                // arrivals, generation, timeout flag, spare
 
 struct CoopArgs {
@@ -896,6 +896,7 @@ struct CoopArgs {
   unsigned* bar;   // GRID_SYNC_WORDS words, zeroed before each launch
   int G;           // CTAs of the launch
   int cap;         // CTAs the slot buffer holds
+  int bar_count;   // CTAs each grid barrier waits for: G (G + 1 only in the timeout test)
 };
 
 // Barrier of all CTAs of a cooperative launch.  Thread 0 of each CTA arrives
@@ -960,7 +961,7 @@ lanczos_step(const __grid_constant__ LaunchParams lp, const __grid_constant__ Co
     double* slots = ca.slots + (iter & 1) * 3 * ca.G;
     pass_body<S, R, TH, DIRI, HAS_V, HAS_AY, true>(lp, &sst, slots, step);
     ++iter;
-    if (!grid_sync(ca.bar, (unsigned)ca.G)) {
+    if (!grid_sync(ca.bar, (unsigned)ca.bar_count)) {
       if (threadIdx.x == 0) { gst->error = ERR_BARRIER; gst->stopped = 1; }
       return;   // psi untouched; the host reports the timeout
     }

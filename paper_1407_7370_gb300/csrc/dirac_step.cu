@@ -37,6 +37,7 @@ cudaError_t launch_step_t(LaunchParams p, int n_sm, CoopArgs ca, cudaStream_t s)
   p.chunk_q = p.total_tiles / grid;
   p.chunk_r = p.total_tiles % grid;
   p.async_tiles = p.chunk_q >= ASYNC_MIN_TILES;
+  ca.bar_count = grid + ca.bar_count;   // ca.bar_count comes in as the extra arrivals to wait for
   ca.G = grid;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);

@@ -244,6 +244,26 @@ def test_kernel_launch_count(precision, mode, per_step):
     assert prop.kernel_launches == 1 + 3 * per_step     # the probe, then the steps
 
 
+def test_one_launch_barrier_timeout_is_reported_and_the_context_recovers():
+    """Every grid-barrier wait of the one-launch step is bounded: a step whose
+    barriers wait for one CTA more than the launch has ends with DIRAC_ECUDA
+    after about a second, psi untouched, and the next steps are correct."""
+    from paper_1407_7370_gb300 import Propagator
+    from paper_1407_7370_gb300 import _native as nat
+    g = wl.Grid(64, 48, 0.1, 0.1)
+    psi0 = wl.positive_energy_packet(g, p0=(4.0, 1.0))
+    prop = Propagator(g.nx, g.ny, g.dx, g.dy, m_max=10)
+    prop.set_fields()
+    psi = torch.from_numpy(psi0.copy()).cuda()
+    st = nat.lib().dirac_debug_barrier_timeout(prop._ctx, ctypes.c_void_p(psi.data_ptr()), 1e-4, 10)
+    assert st == nat.ECUDA
+    assert b"barrier" in nat.lib().dirac_last_error()
+    assert np.array_equal(psi.cpu().numpy(), psi0)
+    prop.steps(psi, 3, 1e-4, 10)
+    ref, _, _ = gpu_run(g, psi0, 1e-4, 10, 3)
+    assert lz.rel_l2(psi.cpu().numpy(), ref) <= 1e-14
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("nx,ny,order,boundary,hasv,tol", [(45, 37, 2, "periodic", True, 0.0),
                                                            (70, 33, 4, "dirichlet", False, 0.0),
