@@ -271,10 +271,12 @@ __device__ inline void finish_pass(const LaunchParams& lp, const Problem* pr, De
   const int lane = threadIdx.x & 31;
   const double shift = pr->shift;
   const bool ok = isfinite(P) && isfinite(Y) && isfinite(X) && X > 0.0;
+  // psi = 0 exactly: exp(-i H dt) 0 = 0, a step that changes nothing
+  const bool zero = X == 0.0 && P == 0.0 && Y == 0.0;
   if (lp.probe) {   // Rayleigh quotient of psi: the first stencil shift
     if (lane == 0) {
-      if (ok) {
-        const double s1 = P / X;   // the probe ran with stencil shift 0
+      if (ok || zero) {
+        const double s1 = ok ? P / X : 0.0;   // the probe ran with stencil shift 0
         st->sigma[1] = s1;
         st->pc_cur = make_coef(1.0, 0.0, 0.0, lp.mcc - shift - s1, -lp.mcc - shift - s1);
         st->cur_pass = 1;
@@ -283,6 +285,26 @@ __device__ inline void finish_pass(const LaunchParams& lp, const Problem* pr, De
       } else {
         st->error = ERR_NONFINITE; st->stopped = 1;
       }
+    }
+    return;
+  }
+  if (zero && i == 1) {   // recombination with C_1 = 0 keeps psi = 0
+    if (lane == 0) {
+      st->nu[1] = 0.0;
+      st->inv_nu[1] = 0.0;
+      st->alpha[1] = st->sigma[1];
+      st->beta[1] = 0.0;
+      st->coef_re[1] = 0.0;
+      st->coef_im[1] = 0.0;
+      st->psi_norm = 0.0;
+      st->energy = 0.0;          // no state, no energy
+      st->err_est = 0.0;
+      st->k_used = 1;
+      st->breakdown = 1;
+      st->beta_last = 0.0;
+      st->pc_cur = make_coef(1.0, 0.0, 0.0, lp.mcc - shift - st->sigma[1], -lp.mcc - shift - st->sigma[1]);
+      st->sigma_valid = 1;
+      st->stopped = 1;
     }
     return;
   }

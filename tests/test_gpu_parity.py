@@ -244,6 +244,48 @@ def test_kernel_launch_count(precision, mode, per_step):
     assert prop.kernel_launches == 1 + 3 * per_step     # the probe, then the steps
 
 
+@pytest.mark.parametrize("precision,mode", [("fp64", "one_launch"), ("fp64", "passes"),
+                                            ("mixed", "passes"), ("mixed", "one_launch")])
+@pytest.mark.parametrize("m", [1, 2, 32])
+def test_krylov_dimension_extremes(precision, mode, m):
+    """m = 1 (psi' = exp(-i alpha_1 dt) psi), m = 2 and the largest Krylov
+    dimension the device recurrence holds (32, one warp), against the oracle."""
+    g = wl.Grid(40, 36, 0.1, 0.1)
+    psi0 = wl.positive_energy_packet(g, p0=(6.0, 2.0)) + 0.02 * wl.random_spinor(g, 5)
+    V = wl.soft_core(g, 1.5)
+    shift = C * C if precision == "mixed" else 0.0
+    dt = 2e-4 if m > 2 else 2e-6
+    out, info, _ = gpu_run(g, psi0, dt, m, 3, V=V, A=(3.0, -1.0), shift=shift, precision=precision,
+                           step_mode=mode)
+    op = oracle_op(g, V=V, A=(3.0, -1.0), shift=shift)
+    ref = psi0.copy()
+    for _ in range(3):
+        ref, oi = lz.krylov_step(op, ref, dt, m)
+    assert info.k_used == oi.k_used == m
+    tol = fp64_tol(3, dt) if precision == "fp64" else mixed_tol(3, dt, hnorm(g, (3.0, -1.0), V))
+    assert lz.rel_l2(out, ref) <= tol
+
+
+@pytest.mark.parametrize("precision,mode", [("fp64", "one_launch"), ("fp64", "passes"),
+                                            ("mixed", "passes")])
+def test_zero_state_stays_zero(precision, mode):
+    """exp(-i H dt) 0 = 0: a zero state is a valid input, not an error."""
+    g = wl.Grid(33, 20, 0.1, 0.1)
+    psi0 = np.zeros((g.ny, g.nx, 2), complex)
+    out, info, prop = gpu_run(g, psi0, 1e-4, 8, 3, A=(1.0, 0.5), precision=precision, step_mode=mode)
+    assert not np.any(out)
+    assert info.norm == 0.0 and info.k_used == 1 and info.err_est == 0.0
+    # and the context goes on with a real state
+    psi1 = wl.positive_energy_packet(g, p0=(3.0, 0.0))
+    psi = torch.from_numpy(psi1.copy()).cuda()
+    prop.steps(psi, 2, 1e-4, 8)
+    ref, _, _ = gpu_run(g, psi1, 1e-4, 8, 2, A=(1.0, 0.5), precision=precision, step_mode=mode)
+    # the first real step starts from the zero state's stencil shift and
+    # re-runs its first pass with the Rayleigh quotient: same T to rounding
+    tol = 1e-12 if precision == "fp64" else mixed_tol(2, 1e-4, hnorm(g, (1.0, 0.5)))
+    assert lz.rel_l2(psi.cpu().numpy(), ref) <= tol
+
+
 def test_one_launch_barrier_timeout_is_reported_and_the_context_recovers():
     """Every grid-barrier wait of the one-launch step is bounded: a step whose
     barriers wait for one CTA more than the launch has ends with DIRAC_ECUDA
