@@ -441,9 +441,24 @@ __host__ __device__ constexpr int rows_per_thread() { return (sizeof(S) == sizeo
 template <class S>
 __host__ __device__ constexpr int sub_workers() { return sizeof(S) == sizeof(double) ? 2 : 1; }
 
-// shared memory of one tile worker: the tile of q^_i with its halo
+// shared memory of one tile worker: the tile of q^_i with its halo, and on
+// the mixed path the staging buffer of q^_{i-1} on the same rectangle
 template <class S, int R, int TH>
 __host__ __device__ constexpr size_t tile_bytes() { return sizeof(S) * 4 * (TH + 2 * R) * (TILE_W + 2 * R); }
+template <class S, int R, int TH>
+__host__ __device__ constexpr size_t qbuf_bytes() {
+  return sizeof(S) == sizeof(float) ? sizeof(float4) * (TH + 2 * R) * (TILE_W + 2 * R) : 0;
+}
+template <class S, int R, int TH>
+__host__ __device__ constexpr size_t worker_bytes() { return tile_bytes<S, R, TH>() + qbuf_bytes<S, R, TH>(); }
+
+// tile workers per CTA of the one-launch step: one CTA per SM on both paths
+// (two workers of eight warps on FP64; 1024 threads of 128-thread workers on
+// FP32), so that a grid barrier and its partial sums involve one CTA per SM
+template <class S, int TH>
+__host__ __device__ constexpr int step_workers() {
+  return sizeof(S) == sizeof(double) ? 2 : 1024 / (32 * (TH / 4));
+}
 
 // Chunks of the tile list: CTA c takes q + 1 tiles if c < r, else q (q = T / G,
 // r = T % G), starting at c q + min(c, r).  The CTA whose chunk holds tile t:
@@ -455,7 +470,7 @@ __device__ __forceinline__ int cta_of_tile(int t, int q, int r) {
 // shared memory of the tile workers: a static array for one worker, the
 // dynamic allocation for several (more than the 48 KiB of static memory)
 template <class S, int R, int TH, int SUB>
-__host__ __device__ constexpr size_t dyn_smem_bytes() { return SUB == 1 ? 0 : SUB * tile_bytes<S, R, TH>(); }
+__host__ __device__ constexpr size_t dyn_smem_bytes() { return SUB == 1 ? 0 : SUB * worker_bytes<S, R, TH>(); }
 
 // The body of one pass over this CTA's chunk.  COOP = false: a launch of
 // its own (lanczos_pass): per-problem tickets, the last CTA finishes.
@@ -463,12 +478,11 @@ __host__ __device__ constexpr size_t dyn_smem_bytes() { return SUB == 1 ? 0 : SU
 // state read from `coop_st`, coherent loads, and the CTA's partial sums
 // written to coop_slots[3 * blockIdx.x ...]; the caller synchronises the grid
 // and finishes.
-template <class S, int R, int TH, bool DIRI, bool HAS_V, bool HAS_AY, bool COOP>
+template <class S, int R, int TH, bool DIRI, bool HAS_V, bool HAS_AY, bool COOP, int SUB>
 __device__ __forceinline__ void pass_body(const LaunchParams& lp, const DevState* coop_st, double* coop_slots,
                                           int step) {
   using T4 = typename Vec4<S>::T;           // storage of y^ (and of q^ on the mixed path)
   constexpr int RPT = rows_per_thread<S, TH>();
-  constexpr int SUB = sub_workers<S>();     // tile workers
   constexpr int NG = TH / RPT;              // row groups = warps of a worker
   constexpr int NTS = 32 * NG;              // threads of a worker
   constexpr int NT = SUB * NTS;             // threads
@@ -488,10 +502,13 @@ __device__ __forceinline__ void pass_body(const LaunchParams& lp, const DevState
   constexpr bool F32 = sizeof(S) == sizeof(float);
   __shared__ __align__(32) S tile_s[SUB == 1 ? TH + 2 * R : 1][W][4];
   S(*const tile)[W][4] = SUB == 1 ? &tile_s[0]
-                                  : reinterpret_cast<S(*)[W][4]>(dyn_smem + sub * tile_bytes<S, R, TH>());
+                                  : reinterpret_cast<S(*)[W][4]>(dyn_smem + sub * worker_bytes<S, R, TH>());
   // mixed path, passes >= 3: q^_{i-1} on the tile and halo, copied asynchronously
-  constexpr int NSQ = F32 ? (TH + 2 * R) * W : 1;
-  __shared__ __align__(16) float4 qbuf[NSQ];
+  constexpr int NSQ = (F32 && SUB == 1) ? (TH + 2 * R) * W : 1;
+  __shared__ __align__(16) float4 qbuf_s[NSQ];
+  float4* const qbuf = SUB == 1 ? qbuf_s
+                                : reinterpret_cast<float4*>(dyn_smem + sub * worker_bytes<S, R, TH>() +
+                                                            tile_bytes<S, R, TH>());
   // barrier of this worker's threads (the whole CTA when there is one worker)
   auto sub_sync = [&]() {
     if constexpr (SUB == 1) {
@@ -662,11 +679,11 @@ __device__ __forceinline__ void pass_body(const LaunchParams& lp, const DevState
       constexpr int NS = (TH + 2 * R) * W;
       float4* const tf = reinterpret_cast<float4*>(&tile[0][0][0]);
       const float4* const qsrc = static_cast<const float4*>(q_prev);
-      for (int tt = t; tt < seg_end; ++tt) {
+      for (int tt = t + sub; tt < seg_end; tt += SUB) {
         const int lt = tt - pr->tile_begin;
         const int x0 = (lt % pr->tiles_x) * TILE_W;
         const int y0 = (lt / pr->tiles_x) * TH;
-        for (int e = threadIdx.x; e < NS; e += NT) {
+        for (int e = ltid; e < NS; e += NTS) {
           const int r = e / W, c = e - r * W;
           bool ox, oy;
           const int ix = wrap<DIRI>(x0 - R + c, nx, ox), iy = wrap<DIRI>(y0 - R + r, ny, oy);
@@ -676,18 +693,18 @@ __device__ __forceinline__ void pass_body(const LaunchParams& lp, const DevState
           cp_async16(qbuf + e, qsrc + idx, in ? 16 : 0);
         }
         cp_async_commit_wait();
-        __syncthreads();
-        for (int e = threadIdx.x; e < NS; e += NT) {
+        sub_sync();
+        for (int e = ltid; e < NS; e += NTS) {
           const float4 yv = tf[e], qp = qbuf[e];
           tf[e] = make_float4(fmaf(-(float)gdS, qp.x, (float)gS * yv.x), fmaf(-(float)gdS, qp.y, (float)gS * yv.y),
                               fmaf(-(float)gdS, qp.z, (float)gS * yv.z), fmaf(-(float)gdS, qp.w, (float)gS * yv.w));
         }
-        __syncthreads();
+        sub_sync();
         stencil_rows(x0, y0, [&](int, int r, int c, S (&qp)[4]) {
           const float4 v = qbuf[r * W + c];
           qp[0] = (S)v.x; qp[1] = (S)v.y; qp[2] = (S)v.z; qp[3] = (S)v.w;
         });
-        __syncthreads();   // tile and qbuf are reused next
+        sub_sync();   // tile and qbuf are reused next
       }
      }
     }
@@ -739,7 +756,7 @@ __device__ __forceinline__ void pass_body(const LaunchParams& lp, const DevState
       double s0 = 0.0, s1 = 0.0, s2 = 0.0;
       if (lane < NW) { s0 = red[lane][0]; s1 = red[lane][1]; s2 = red[lane][2]; }
 #pragma unroll
-      for (int o = 8; o > 0; o >>= 1) {   // NW <= 16 warps
+      for (int o = (NW > 16 ? 16 : 8); o > 0; o >>= 1) {   // NW <= 32 warps
         s0 += __shfl_xor_sync(0xffffffffu, s0, o);
         s1 += __shfl_xor_sync(0xffffffffu, s1, o);
         s2 += __shfl_xor_sync(0xffffffffu, s2, o);
@@ -809,7 +826,7 @@ lanczos_pass(const __grid_constant__ LaunchParams lp) {
   // programmatic dependent launch: nothing the previous kernel wrote is read
   // before this point
   asm volatile("griddepcontrol.wait;" ::: "memory");
-  pass_body<S, R, TH, DIRI, HAS_V, HAS_AY, false>(lp, nullptr, nullptr, *lp.step);
+  pass_body<S, R, TH, DIRI, HAS_V, HAS_AY, false, sub_workers<S>()>(lp, nullptr, nullptr, *lp.step);
   // the next kernel may be scheduled now (it waits for our completion)
   asm volatile("griddepcontrol.launch_dependents;");
 }
@@ -958,11 +975,11 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned G) {
 }
 
 template <class S, int R, int TH, bool DIRI, bool HAS_V, bool HAS_AY>
-__global__ void __launch_bounds__(sub_workers<S>() * 32 * (TH / rows_per_thread<S, TH>()),
-                                  (min_blocks<S, TH, sub_workers<S>()>()))
+__global__ void __launch_bounds__(step_workers<S, TH>() * 32 * (TH / rows_per_thread<S, TH>()), 1)
 lanczos_step(const __grid_constant__ LaunchParams lp, const __grid_constant__ CoopArgs ca) {
   constexpr bool F32 = sizeof(S) == sizeof(float);
-  constexpr int NT = sub_workers<S>() * 32 * (TH / rows_per_thread<S, TH>());
+  constexpr int SUB = step_workers<S, TH>();
+  constexpr int NT = SUB * 32 * (TH / rows_per_thread<S, TH>());
   __shared__ DevState sst;
   __shared__ double cr_s[KMAX + 2], ci_s[KMAX + 2];
   __shared__ float fr_s[KMAX + 2], fi_s[KMAX + 2];
@@ -981,7 +998,7 @@ lanczos_step(const __grid_constant__ LaunchParams lp, const __grid_constant__ Co
   while (!sst.stopped && iter < max_iter) {
     const int i = max(1, sst.cur_pass);
     double* slots = ca.slots + (iter & 1) * 3 * ca.G;
-    pass_body<S, R, TH, DIRI, HAS_V, HAS_AY, true>(lp, &sst, slots, step);
+    pass_body<S, R, TH, DIRI, HAS_V, HAS_AY, true, SUB>(lp, &sst, slots, step);
     ++iter;
     if (!grid_sync(ca.bar, (unsigned)ca.bar_count)) {
       if (threadIdx.x == 0) { gst->error = ERR_BARRIER; gst->stopped = 1; }

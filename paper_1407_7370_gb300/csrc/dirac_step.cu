@@ -18,8 +18,9 @@ namespace {
 template <class S, int R, int TH, bool D, bool V, bool AY>
 cudaError_t launch_step_t(LaunchParams p, int n_sm, CoopArgs ca, cudaStream_t s) {
   static int occ = 0;
-  constexpr int NT = sub_workers<S>() * 32 * (TH / rows_per_thread<S, TH>());
-  constexpr size_t smem = dyn_smem_bytes<S, R, TH, sub_workers<S>()>();
+  constexpr int SUB = step_workers<S, TH>();
+  constexpr int NT = SUB * 32 * (TH / rows_per_thread<S, TH>());
+  constexpr size_t smem = dyn_smem_bytes<S, R, TH, SUB>();
   if (occ == 0) {
     cudaError_t e = cudaSuccess;
     if (smem > 0) {
