@@ -286,6 +286,29 @@ def test_zero_state_stays_zero(precision, mode):
     assert lz.rel_l2(psi.cpu().numpy(), ref) <= tol
 
 
+@pytest.mark.parametrize("mode", ["one_launch", "passes"])
+def test_pass_rerun_after_a_far_stencil_shift(mode):
+    """A step of the zero state leaves the first stencil shift at 0; the next
+    state is a plane-wave eigenvector plus 1e-7 noise, so ||y^||^2 / s2 of its
+    first pass is ~1e13 (beyond the FP64 limit of 1e12): the device re-runs
+    the pass with sigma = alpha_1 and the step still matches the oracle."""
+    from paper_1407_7370_gb300 import Propagator
+    from tests.test_oracle_hamiltonian import plane_wave_eigpair
+    g = wl.Grid(32, 24, 0.1, 0.1)
+    pw, _ = plane_wave_eigpair(g.nx, g.ny, g.dx, g.dy, 2, 1, 2, (0.0, 0.0), 0.0)
+    psi1 = pw + 1e-7 * wl.random_spinor(g, 21)
+    prop = Propagator(g.nx, g.ny, g.dx, g.dy, m_max=8)
+    prop.set_step_mode(mode)
+    prop.set_fields()
+    zero = torch.zeros((g.ny, g.nx, 2), dtype=torch.complex128, device="cuda")
+    prop.steps(zero, 1, 1e-4, 8)
+    psi = torch.from_numpy(psi1.copy()).cuda()
+    info = prop.steps(psi, 1, 1e-4, 8, info=True)
+    assert info.kappa_max > 1e12          # the pass was re-run
+    ref, _ = lz.krylov_step(oracle_op(g), psi1.copy(), 1e-4, 8)
+    assert lz.rel_l2(psi.cpu().numpy(), ref) <= fp64_tol(1, 1e-4)
+
+
 def test_one_launch_barrier_timeout_is_reported_and_the_context_recovers():
     """Every grid-barrier wait of the one-launch step is bounded: a step whose
     barriers wait for one CTA more than the launch has ends with DIRAC_ECUDA
