@@ -39,7 +39,7 @@ CFG = wl.LASER_PACKET_1024
 SITE_BYTES = 32            # complex128 spinor
 PASS_BYTES_PER_SITE = 3 * SITE_BYTES   # read q_i, read q_{i-1}, write q_{i+1} (V = 0)
 PASS_BYTES_PER_SITE_MIXED = 3 * 16      # the same accesses in complex64
-PASS_FLOPS_PER_SITE = 80   # FP64 flops of one Lanczos iteration per site
+PASS_FLOPS_PER_SITE = 80   # FP64 flops of one Lanczos iteration per site: stencil 44, -beta q 8, two dot products 16, normalisation 12
 RECOMB_FLOPS_PER_VECTOR = 16   # psi += C_j q_j: a complex multiply-add on both spinor components
 
 
@@ -599,7 +599,7 @@ def run_ours(args):
     # FP64 path: bound by the FP64 pipe
     f = runs["fp64"]
     fk = kernel_stats(f)
-    fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12   # TFLOP/s, see the design doc
+    fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12   # TFLOP/s: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz
     if fk["one_launch"]:
         f_kernel = "lanczos_step<double>"
         f_flops_site = (PASS_FLOPS_PER_SITE + RECOMB_FLOPS_PER_VECTOR) * m   # one launch = one step

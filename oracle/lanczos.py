@@ -5,7 +5,7 @@ Sec. 2 (Fig. 1 with the modified Gram-Schmidt alpha of Eq. 4), Sec. 4
 estimate Eq. 18), Sec. 6 (cumulative error bound), Sec. 2/5 (Ritz values,
 the bound Eq. 9, full reorthogonalisation applied twice).
 
-Readings where the paper leaves a choice (each also listed in the design doc):
+Readings where the paper leaves a choice:
 
 * A is the Hermitian matrix of the integral of H over the step (Sec. 4); with
   the first Magnus term and H affine in the field, that is dt * H(A_mean).
