@@ -306,6 +306,8 @@ def measure_batch(args, torch, world, dist, gi, pk):
         tune = bp.autotune(psis, dt, m, A=A[:3], steps=3)
         bp.steps(psis, W, dt, m, A=A[:W])
         torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
         clocks = ClockSampler(gi)
         clocks.start()
         l0 = bp.kernel_launches
@@ -317,7 +319,7 @@ def measure_batch(args, torch, world, dist, gi, pk):
         torch.cuda.synchronize()
         launches = bp.kernel_launches - l0
         clk = clocks.stop()
-        t = e0.elapsed_time(e1) / 1e3
+        t = max_over_ranks(e0.elapsed_time(e1) / 1e3, world, dist, "cuda")   # the slowest replica
         bp.profile(True)
         bp.steps(psis, steps, dt, m, A=A[W + steps:W + 2 * steps])
         prof = bp.profile_read()
