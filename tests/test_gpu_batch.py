@@ -158,3 +158,41 @@ def test_autotune_leaves_states_and_picks_a_shape(tmp_path, monkeypatch):
     op = ham.Operator(grid.nx, grid.ny, grid.dx, grid.dy, V=V)
     ref, _ = lz.propagate(op, psi0.copy(), 1e-4, 8, 2)
     assert lz.rel_l2(psis[0].cpu().numpy(), ref) <= mixed_tol(2, 1e-4, hnorm(grid, np.zeros((1, 2)), V))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_batch_256_full_size_sampled(precision):
+    """The batched workload at its full size (256 packets on 128^2..512^2
+    grids, m = 16, laser amplitudes up to 100 au), autotuned and replayed as
+    a graph as the benchmark runs it: one problem of every grid size against
+    the oracle run alone (its own step means of the pulse)."""
+    from oracle import fields
+    from paper_1407_7370_gb300 import BatchPropagator
+    from paper_1407_7370_gb300.propagator import pulse_sin2_mean
+    cfg = wl.BATCH_256
+    grids, p0s, a0s = wl.batch_packets(cfg["n"])
+    m, dt, n, pulse = cfg["m"], cfg["dt"], cfg["n"], cfg["pulse"]
+    steps, C2 = 2, 137.036 ** 2
+    t0 = 0.5   # mid-pulse, where A_x reaches a few au
+    base = np.array([pulse_sin2_mean(t0 + k * dt, dt, 1.0, pulse.omega, pulse.duration) for k in range(3)])
+    A = np.zeros((3, n, 2))
+    A[:, :, 0] = base[:, None] * a0s[None, :]
+    bp = BatchPropagator([(g.nx, g.ny, g.dx, g.dy) for g in grids], m_max=m, precision=precision)
+    for k in range(n):
+        bp.set_fields(k, shift=C2)
+    psi0 = [wl.positive_energy_packet(g, p0=(float(p), 0.0)) for g, p in zip(grids, p0s)]
+    psis = [torch.from_numpy(p.copy()).cuda() for p in psi0]
+    bp.autotune(psis, dt, m, A=A, steps=3)
+    bp.steps(psis, steps, dt, m, A=A[:steps])
+    sample = [next(k for k, g in enumerate(grids) if g.nx == side) for side in (128, 256, 384, 512)]
+    for k in sample:
+        g = grids[k]
+        op = ham.Operator(g.nx, g.ny, g.dx, g.dy, shift=C2)
+        ref = psi0[k]
+        for s in range(steps):
+            op.A = (a0s[k] * fields.step_mean(pulse, t0 + s * dt, dt), 0.0)
+            ref, _ = lz.krylov_step(op, ref, dt, m)
+        err = lz.rel_l2(psis[k].cpu().numpy(), ref)
+        tol = fp64_tol(steps, dt) if precision == "fp64" else mixed_tol(steps, dt, hnorm(g, A[:steps, k]))
+        assert err <= tol, (k, g.nx, err, tol)
