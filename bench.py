@@ -617,6 +617,9 @@ def run_ours(args):
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz "
                                "(probe measured 1.19 TFLOP/s)"}
     f_gbs = f_bytes_site * g.n_sites / fk["launch_s"] / 1e9
+    if roofline["traffic"] is not None:   # the ncu DRAM bytes of a launch over its live duration
+        roofline["dram_gbs"] = roofline["traffic"] / fk["launch_s"] / 1e9
+        roofline["dram_frac_of_hbm"] = roofline["dram_gbs"] / hbm_peak
     # mixed path: bound by HBM
     x = runs["mixed"]
     xk = kernel_stats(x)
@@ -625,12 +628,14 @@ def run_ours(args):
     else:
         x_kernel, x_bytes_site = "lanczos_pass<float>", PASS_BYTES_PER_SITE_MIXED
     x_gbs = x_bytes_site * g.n_sites / xk["launch_s"] / 1e9
+    x_traffic = traffic_for(x_kernel, g)
     err = float(torch.linalg.vector_norm(x["result"] - f["result"]) /
                 torch.linalg.vector_norm(f["result"]))
     mixed = {"value": site_rate(x["t"], K), "unit": UNIT, "ms_per_step": 1e3 * x["t"] / K,
              "dtype": "f32 stencil/basis + f64 scalars and state",
              "roofline": {"bound": "hbm", "achieved": x_gbs, "peak": hbm_peak, "unit": "GB/s",
-                          "frac": x_gbs / hbm_peak, "traffic": traffic_for(x_kernel, g),
+                          "frac": x_gbs / hbm_peak, "traffic": x_traffic,
+                          "dram_gbs": None if x_traffic is None else x_traffic / xk["launch_s"] / 1e9,
                           "kernel": x_kernel, "kernel_avg_us": xk["launch_s"] * 1e6,
                           "kernel_share": xk["share"], "peak_source": hbm_src,
                           "bytes_per_site": x_bytes_site},
