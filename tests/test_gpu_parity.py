@@ -383,6 +383,40 @@ def test_laser_packet_1024_full_size():
     assert abs(ham.norm(out) - ham.norm(psi0)) <= 1e-12 * ham.norm(psi0)
 
 
+_LONG_RUN = {}
+
+
+def _long_run_exact(n, t0):
+    """Closed-form propagation of the 1024^2 laser packet (cached: one CPU run
+    serves both precisions)."""
+    key = (n, t0)
+    if key not in _LONG_RUN:
+        cfg = wl.LASER_PACKET_1024
+        g = cfg["grid"]
+        psi0 = wl.positive_energy_packet(g, p0=cfg["p0"], sigma_x=cfg["sigma_x"])
+        _LONG_RUN[key] = (psi0, free.propagate(oracle_op(g), psi0.copy(), cfg["dt"], n, pulse=cfg["pulse"],
+                                               t0=t0))
+    return _LONG_RUN[key]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_laser_packet_1024_long_run_against_closed_form(precision):
+    """200 steps (0.04 au of simulated time) of the benchmark's workload
+    against the closed-form propagation in Fourier space, with the targets
+    per unit of simulated time: 1e-10 (FP64) and 1e-5 (mixed)."""
+    from paper_1407_7370_gb300.propagator import pulse_schedule
+    cfg = wl.LASER_PACKET_1024
+    g, p = cfg["grid"], cfg["pulse"]
+    dt, m, t0, n = cfg["dt"], cfg["m"], 0.3, 200
+    psi0, exact = _long_run_exact(n, t0)
+    An = pulse_schedule(t0, dt, n, p.a0, p.omega, p.duration)
+    shift = C * C if precision == "mixed" else 0.0
+    out, info, _ = gpu_run(g, psi0, dt, m, n, A_steps=An, precision=precision, shift=shift)
+    target = (1e-10 if precision == "fp64" else 1e-5) * n * dt
+    assert lz.rel_l2(out, exact) <= target
+
+
 # ---------------------------------------------------------------------------
 # Mixed path: complex64 basis and FP32 stencil, FP64 scalars and state.
 # Tolerance: relative L2 of psi at most 1e-5 per unit of simulated time
