@@ -20,8 +20,10 @@
  *  - all work is enqueued on the context's CUDA stream and is asynchronous
  *    unless a call says it synchronises.
  *  - no call aborts or throws; each returns a dirac_status.  Device-side
- *    failures (non-finite values) are recorded on the device and returned by
- *    the next call that synchronises (an info request, dirac_sync).
+ *    failures (non-finite values: DIRAC_ENONFINITE; a timed-out grid barrier
+ *    of the one-launch step: DIRAC_ECUDA) are recorded on the device and
+ *    returned by the next call that synchronises (an info request,
+ *    dirac_sync); psi is left unchanged and the context stays usable.
  *  - the caller owns every buffer it passes; the library owns the context
  *    and its workspace (the Krylov basis lives in device memory).
  */
@@ -114,7 +116,8 @@ dirac_status dirac_set_vector_potential(dirac_ctx* ctx, double A_x, double A_y);
  * Krylov space of dimension m (1..m_max).  tol > 0 stops the recurrence at the
  * first k whose Eq. 18 estimate is <= tol * ||psi||; tol = 0 always uses m
  * (unless the recurrence breaks down, beta_k <= 1e-12 times the largest
- * |alpha_j + s| or beta_j so far).  psi_dev: device complex128 [ny][nx][2],
+ * |alpha_j + s| or beta_j so far).  A zero psi stays zero (k_used = 1,
+ * norm 0, no error).  psi_dev: device complex128 [ny][nx][2],
  * 32-byte aligned, owned by the caller.  If info is non-NULL the call
  * synchronises the stream and fills it; otherwise it returns after enqueueing.
  * dt < 0 steps backwards in time, psi <- exp(+i H |dt|) psi (T is real, so
@@ -122,7 +125,8 @@ dirac_status dirac_set_vector_potential(dirac_ctx* ctx, double A_x, double A_y);
  * Errors: DIRAC_EINVAL (m out of range, dt = 0 or non-finite, tol < 0,
  * misaligned psi, dt too large for the small exponential: |dt| ||H|| > 90),
  * DIRAC_ESTATE (no set_fields yet), DIRAC_ENONFINITE (only with info),
- * DIRAC_ECUDA.
+ * DIRAC_ECUDA (a CUDA call failed, or -- only with info -- a grid barrier
+ * of the one-launch step timed out).
  */
 dirac_status dirac_lanczos_step(dirac_ctx* ctx, void* psi_dev, double dt, int m, double tol,
                                 dirac_step_info* info);
