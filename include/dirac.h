@@ -152,6 +152,22 @@ dirac_status dirac_propagate_host(dirac_ctx* ctx, void* psi_host, int nsteps, do
 /* Wait for the context's stream; returns a pending device error if any. */
 dirac_status dirac_sync(dirac_ctx* ctx);
 
+/*
+ * Checkpoint and resume.  Between steps a context carries, besides psi, a
+ * small device block of scalars from step to step (the next step's stencil
+ * shift, the cumulative Eq. 18 estimate, ...).  dirac_export_state copies it
+ * to a host buffer of dirac_state_bytes(ctx) bytes (synchronises; DIRAC_ESTATE
+ * before the first step); dirac_import_state loads it into a context created
+ * with the same arguments by the same library build, after its
+ * dirac_set_fields (which otherwise re-derives the shift from psi).  With the
+ * same fields and psi, the resumed context then computes bitwise what the
+ * original would have.  The block is opaque.  Errors: DIRAC_EINVAL (sizes, a block not
+ * exported between steps), DIRAC_ECUDA.
+ */
+size_t dirac_state_bytes(const dirac_ctx* ctx);
+dirac_status dirac_export_state(dirac_ctx* ctx, void* host, size_t bytes);
+dirac_status dirac_import_state(dirac_ctx* ctx, const void* host, size_t bytes);
+
 /* Mean of A_x(t) = a0 sin^2(pi t/T) sin(omega t) (zero outside [0, T]) over
  * [t0, t0 + dt], in closed form: the first Magnus term of Eq. 16. */
 double dirac_pulse_sin2_mean(double t0, double dt, double a0, double omega, double duration);

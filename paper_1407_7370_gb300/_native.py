@@ -103,6 +103,9 @@ def lib():
         "dirac_lanczos_steps": (i, [vp, vp, i, d, i, d, dp, ctypes.POINTER(StepInfoC)]),
         "dirac_propagate_host": (i, [vp, vp, i, d, i, d, dp, ctypes.POINTER(StepInfoC)]),
         "dirac_sync": (i, [vp]),
+        "dirac_state_bytes": (ctypes.c_size_t, [vp]),
+        "dirac_export_state": (i, [vp, vp, ctypes.c_size_t]),
+        "dirac_import_state": (i, [vp, vp, ctypes.c_size_t]),
         "dirac_pulse_sin2_mean": (d, [d, d, d, d, d]),
         "dirac_pulse_sine_basis_means": (i, [i, d, i, d, dp]),
         "dirac_kernel_launches": (ctypes.c_longlong, [vp]),

@@ -943,6 +943,37 @@ dirac_status dirac_sync(dirac_ctx* ctx) {
   return ctx->e.read_state(nullptr);
 }
 
+size_t dirac_state_bytes(const dirac_ctx* ctx) {
+  return ctx ? sizeof(DevState) * ctx->e.P.size() : 0;
+}
+
+dirac_status dirac_export_state(dirac_ctx* ctx, void* host, size_t bytes) {
+  if (!ctx || !host) return fail(DIRAC_EINVAL, "null context or buffer");
+  Engine& e = ctx->e;
+  if (bytes != sizeof(DevState) * e.P.size()) return fail(DIRAC_EINVAL, "state buffer of %zu bytes, need %zu",
+                                                           bytes, sizeof(DevState) * e.P.size());
+  if (e.need_probe) return fail(DIRAC_ESTATE, "no step has run since the context was created or re-armed");
+  dirac_status s = e.read_state(nullptr);   // waits, and reports a pending device error
+  if (s != DIRAC_OK) return s;
+  std::memcpy(host, e.h_st, bytes);
+  return DIRAC_OK;
+}
+
+dirac_status dirac_import_state(dirac_ctx* ctx, const void* host, size_t bytes) {
+  if (!ctx || !host) return fail(DIRAC_EINVAL, "null context or buffer");
+  Engine& e = ctx->e;
+  if (bytes != sizeof(DevState) * e.P.size()) return fail(DIRAC_EINVAL, "state buffer of %zu bytes, need %zu",
+                                                           bytes, sizeof(DevState) * e.P.size());
+  const DevState* st = static_cast<const DevState*>(host);
+  for (size_t b = 0; b < e.P.size(); ++b)
+    if (st[b].error || st[b].stopped || !st[b].sigma_valid || st[b].cur_pass != 1)
+      return fail(DIRAC_EINVAL, "not a state exported between steps");
+  CUDA_TRY(cudaStreamSynchronize(e.stream));
+  CUDA_TRY(cudaMemcpy(e.d_st, host, bytes, cudaMemcpyHostToDevice));
+  e.need_probe = false;   // the imported stencil shift is the one the next step uses
+  return DIRAC_OK;
+}
+
 double dirac_pulse_sin2_mean(double t0, double dt, double a0, double omega, double duration) {
   // sin^2(pi t/T) sin(w t) = sin(w t)/2 - sin((w+W) t)/4 - sin((w-W) t)/4, W = 2 pi / T
   if (!(dt > 0.0) || !(duration > 0.0)) return 0.0;

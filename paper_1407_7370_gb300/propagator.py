@@ -236,6 +236,19 @@ class Propagator:
     def use_graphs(self, enable: bool = True):
         nat.check(nat.lib().dirac_use_graphs(self._ctx, 1 if enable else 0))
 
+    def export_state(self) -> bytes:
+        """The device scalars carried between steps (see dirac_export_state):
+        with psi, a checkpoint from which import_state resumes bitwise."""
+        L = nat.lib()
+        n = L.dirac_state_bytes(self._ctx)
+        buf = ctypes.create_string_buffer(n)
+        nat.check(L.dirac_export_state(self._ctx, buf, n))
+        return buf.raw
+
+    def import_state(self, state: bytes):
+        buf = ctypes.create_string_buffer(state, len(state))
+        nat.check(nat.lib().dirac_import_state(self._ctx, buf, len(state)))
+
     def set_step_mode(self, mode: str = "auto"):
         """'auto', 'passes' or 'one_launch' (see dirac_set_step_mode)."""
         code = {"auto": nat.STEP_AUTO, "passes": nat.STEP_PASSES, "one_launch": nat.STEP_ONE_LAUNCH}[mode]

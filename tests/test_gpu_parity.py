@@ -309,6 +309,57 @@ def test_pass_rerun_after_a_far_stencil_shift(mode):
     assert lz.rel_l2(psi.cpu().numpy(), ref) <= fp64_tol(1, 1e-4)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_checkpoint_resume_is_bitwise(precision):
+    """psi and the exported scalar block taken between steps let a new
+    context continue bitwise as the original does, cumulative estimate
+    included."""
+    from paper_1407_7370_gb300 import Propagator
+    g = wl.Grid(70, 44, 0.1, 0.1)
+    psi0 = wl.positive_energy_packet(g, p0=(8.0, -3.0))
+    V = wl.soft_core(g, 2.0)
+    rng = np.random.default_rng(4)
+    A = rng.uniform(-10, 10, size=(6, 2))
+    shift = C * C if precision == "mixed" else 0.0
+
+    def fresh():
+        p = Propagator(g.nx, g.ny, g.dx, g.dy, m_max=12, precision=precision)
+        p.set_fields(torch.from_numpy(V).cuda(), shift=shift)
+        return p
+
+    a = fresh()
+    psi = torch.from_numpy(psi0.copy()).cuda()
+    a.steps(psi, 3, 1e-4, 12, A=A[:3])
+    state, ck = a.export_state(), psi.clone()
+    ia = a.steps(psi, 3, 1e-4, 12, A=A[3:], info=True)
+    b = fresh()
+    b.import_state(state)
+    ib = b.steps(ck, 3, 1e-4, 12, A=A[3:], info=True)
+    assert torch.equal(ck, psi)
+    assert ib.cum_err == ia.cum_err and ib.k_used == ia.k_used
+
+
+@pytest.mark.parametrize("nx,ny", [(1, 37), (29, 1), (2, 2), (3, 5)])
+@pytest.mark.parametrize("order,boundary", [(2, "periodic"), (4, "dirichlet")])
+def test_degenerate_thin_grids(nx, ny, order, boundary):
+    """One-site-wide, two-by-two and three-by-five grids: the stencil wraps
+    onto itself (periodic) or sees only zeros (Dirichlet); both launch forms
+    against the oracle."""
+    g = wl.Grid(nx, ny, 0.1, 0.1)
+    psi0 = wl.random_spinor(g, 13)
+    b = ham.DIRICHLET if boundary == "dirichlet" else ham.PERIODIC
+    m = min(6, 2 * nx * ny)
+    op = oracle_op(g, A=(2.0, -1.0), order=order, boundary=b)
+    ref = psi0.copy()
+    for _ in range(3):
+        ref, oi = lz.krylov_step(op, ref, 1e-3, m)
+    for mode in ("one_launch", "passes"):
+        out, info, _ = gpu_run(g, psi0, 1e-3, m, 3, A=(2.0, -1.0), order=order, boundary=boundary,
+                               step_mode=mode)
+        assert info.k_used == oi.k_used
+        assert lz.rel_l2(out, ref) <= fp64_tol(3, 1e-3)
+
+
 def test_one_launch_barrier_timeout_is_reported_and_the_context_recovers():
     """Every grid-barrier wait of the one-launch step is bounded: a step whose
     barriers wait for one CTA more than the launch has ends with DIRAC_ECUDA

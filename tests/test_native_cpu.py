@@ -78,6 +78,9 @@ def test_binding_constants_match_the_header():
 def test_calls_on_null_context_fail_cleanly(lib):
     assert lib.dirac_set_step_mode(None, 0) == nat.EINVAL
     assert lib.dirac_debug_barrier_timeout(None, None, 1e-4, 4) == nat.EINVAL
+    assert lib.dirac_state_bytes(None) == 0
+    assert lib.dirac_export_state(None, None, 0) == nat.EINVAL
+    assert lib.dirac_import_state(None, None, 0) == nat.EINVAL
     assert lib.dirac_set_fields(None, None, 0.0, 0.0, 0.0) == nat.EINVAL
     assert lib.dirac_lanczos_step(None, None, 1e-4, 10, 0.0, None) == nat.EINVAL
     assert lib.dirac_sync(None) == nat.EINVAL
