@@ -6,7 +6,9 @@
   eigenvectors;
 * breakdown on a start vector inside a 3-dimensional invariant subspace:
   three iterations, the exact closed-form energies (free dispersion, Eq. 25
-  on the lattice).
+  on the lattice);
+* loss of orthogonality: ghost copies without reorthogonalisation, none with
+  it (every converged value pairs with its own dense eigenvalue).
 """
 import numpy as np
 import pytest
@@ -108,3 +110,28 @@ def test_breakdown_in_invariant_subspace_gives_exact_energies():
     assert res.breakdown and res.iterations == 3
     assert np.allclose(np.sort(res.all_ritz), np.sort(energies), rtol=1e-12, atol=1e-9)
     assert np.allclose(res.values, np.sort(energies), rtol=1e-12, atol=1e-9)
+
+
+def test_reorthogonalisation_removes_ghost_copies():
+    """Loss of orthogonality (Sec. 2): the plain recurrence, run long enough,
+    returns converged copies of eigenvalues it already found; with the full
+    reorthogonalisation every converged value pairs with its own eigenvalue of
+    the dense operator."""
+    g = wl.Grid(24, 20, 0.3, 0.3)
+    V = wl.soft_core(g, 2.0)
+    start = wl.positive_energy_packet(g, p0=(0.0, 0.0)) + 1e-3 * wl.random_spinor(g, 4)
+    op = ham.Operator(g.nx, g.ny, g.dx, g.dy, V=V, shift=C * C)
+    window = (-C * C, 0.0)
+    exact = np.linalg.eigvalsh(ham.dense(op))
+    exact = exact[(exact > window[0]) & (exact < window[1])]
+
+    def copies(values):
+        # values that share their nearest dense eigenvalue with another value
+        nearest = [int(np.argmin(np.abs(exact - v))) for v in values]
+        return len(nearest) - len(set(nearest))
+
+    full = lz.lanczos_eigs(op, start, n_want=48, max_iter=400, tol=1e-10, window=window)
+    plain = lz.lanczos_eigs(op, start, n_want=48, max_iter=400, tol=1e-10, window=window, reorth=False)
+    assert full.values.size >= 8 and copies(full.values) == 0
+    assert np.max(np.abs(exact[[int(np.argmin(np.abs(exact - v))) for v in full.values]] - full.values)) < 1e-8
+    assert copies(plain.values) >= 1
