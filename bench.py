@@ -87,11 +87,13 @@ def parse():
                     help="grid side of the eigen workload (default: the configured 2048)")
     ap.add_argument("--eigen-iters", type=int, default=None, help="Lanczos iterations of the eigen workload")
     ap.add_argument("--adjoint-steps", type=int, default=None, help="steps of the adjoint workload")
+    ap.add_argument("--no-paper-workload", action="store_true",
+                    help="skip the paper's 8192^2 benchmark shape")
     ap.add_argument("--side", type=int, default=None,
                     help="grid side of the laser-packet workload (profiling; default: the configured 1024)")
     ap.add_argument("--batch-compare-steps", type=int, default=None,
                     help="steps of the batched mixed-vs-FP64 comparison (profiling; default: the configured 2000)")
-    ap.add_argument("--only", choices=["fp64", "mixed", "eigen", "adjoint", "batch"], default=None,
+    ap.add_argument("--only", choices=["fp64", "mixed", "eigen", "adjoint", "batch", "paper"], default=None,
                     help="run one path only (for profiling); prints a partial line")
     return ap.parse_args()
 
@@ -464,6 +466,50 @@ ADJ_CFG = dict(
 CONTRACT_FLOPS_PER_SITE = 16 * 16 * 16   # 8 FMA per (j, l) pair of the two 16-vector bases
 
 
+PAPER_CFG = dict(
+    name="free packet 8192x8192 (the paper's Sec. 7 benchmark shape), dx=1e-3 (not stated in the "
+         "paper), m=10, dt=1e-7, FP64",
+    side=8192, dx=1e-3, m=10, dt=1e-7, p0=100.0, paper_seconds_per_step=120.0)
+
+
+def measure_paper_workload(torch, gi):
+    """The paper's own 2D benchmark shape (Sec. 7): an 8192^2 grid, k = 10
+    Lanczos iterations per step of 1e-7 au, about two minutes per step there.
+    The state is a Gaussian spinor packet with mean momentum (100, 0) au
+    built on the device (the work of a step does not depend on the values).
+    Reported beside the paper's time as context: other hardware."""
+    from paper_1407_7370_gb300 import Propagator
+    c = PAPER_CFG
+    n, dx, m, dt = c["side"], c["dx"], c["m"], c["dt"]
+    x = (torch.arange(n, device="cuda", dtype=torch.float64) - n // 2) * dx
+    env = torch.exp(-(x[None, :] ** 2 + x[:, None] ** 2) / (2 * (20 * dx) ** 2))
+    phase = torch.exp(1j * c["p0"] * x.to(torch.complex128))[None, :]
+    psi = torch.zeros((n, n, 2), dtype=torch.complex128, device="cuda")
+    psi[..., 0] = env * phase
+    psi[..., 1] = 0.05 * env * phase
+    del env, phase, x
+    prop = Propagator(n, n, dx, dx, m_max=m)
+    prop.set_fields(None)
+    prop.steps(psi, 3, dt, m)
+    torch.cuda.synchronize()
+    K = 5
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    e0.record(stream)
+    prop.steps(psi, K, dt, m)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / K
+    prop.close()
+    del psi
+    torch.cuda.empty_cache()
+    return {"workload": c["name"], "ms_per_step": 1e3 * t, "steps": K,
+            "value": n * n * m / t, "unit": UNIT,
+            "paper_seconds_per_step": c["paper_seconds_per_step"],
+            "ratio_to_paper_time": c["paper_seconds_per_step"] / t,
+            "note": "the paper's time is one CPU process on a dual 8-core Xeon-E5 node: context"}
+
+
 def measure_adjoint(torch, gi, pk, steps=None):
     """The adjoint sweep of the 1024^2 gradient workload over `steps` steps (the
     full run is `full_steps` steps at the same cost per step), then a short
@@ -553,11 +599,13 @@ def run_ours(args):
     pk = peaks()
     hbm_peak = pk.get("hbm_gbs", 6800.0)
     hbm_src = "MEASURED_PEAKS.json hbm_gbs (burst copy)" if "hbm_gbs" in pk else "fallback 6.8 TB/s"
-    if args.only in ("eigen", "adjoint", "batch"):   # one workload alone (profiling runs)
+    if args.only in ("eigen", "adjoint", "batch", "paper"):   # one workload alone (profiling runs)
         if args.only == "eigen":
             r = measure_eigen(torch, local, pk, args.eigen_side, args.eigen_iters)
         elif args.only == "adjoint":
             r = measure_adjoint(torch, local, pk, args.adjoint_steps)
+        elif args.only == "paper":
+            r = measure_paper_workload(torch, local)
         else:
             r = measure_batch(args, torch, world, dist, local, pk)
         if rank == 0:
@@ -686,6 +734,8 @@ def run_ours(args):
             line["eigen"] = measure_eigen(torch, local, pk, args.eigen_side, args.eigen_iters)
         if not args.no_adjoint:
             line["adjoint"] = measure_adjoint(torch, local, pk, args.adjoint_steps)
+        if not args.no_paper_workload:
+            line["paper_workload"] = measure_paper_workload(torch, local)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline()
         elif not args.no_cpu_baseline:
