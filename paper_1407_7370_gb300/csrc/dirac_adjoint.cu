@@ -388,6 +388,7 @@ dirac_status dirac_adjoint_gradient(dirac_ctx* ctx, const void* psi0_dev, int ns
                                     const double* A_xy_host, const dirac_adjoint_opts* opts,
                                     double* loss_out, void* psiN_dev, void* dV_dev, double* dA_host,
                                     double* da_host, dirac_adjoint_info* info) {
+  dirac::TraceRange trace("dirac_adjoint_gradient");
   CtxView v;
   ADJ_CHECK(ctx_view(ctx, &v));
   if (!v.fields_set) return fail(DIRAC_ESTATE, "dirac_set_fields has not been called");

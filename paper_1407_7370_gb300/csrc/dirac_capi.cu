@@ -915,6 +915,7 @@ dirac_status dirac_lanczos_step(dirac_ctx* ctx, void* psi_dev, double dt, int m,
 
 dirac_status dirac_lanczos_steps(dirac_ctx* ctx, void* psi_dev, int nsteps, double dt, int m,
                                  double tol, const double* A_xy_host, dirac_step_info* info) {
+  dirac::TraceRange trace("dirac_lanczos_steps");
   if (!ctx) return fail(DIRAC_EINVAL, "null context");
   if (!psi_dev) return fail(DIRAC_EINVAL, "null psi");
   vec4* psi = static_cast<vec4*>(psi_dev);
@@ -926,6 +927,7 @@ dirac_status dirac_lanczos_steps(dirac_ctx* ctx, void* psi_dev, int nsteps, doub
 
 dirac_status dirac_propagate_host(dirac_ctx* ctx, void* psi_host, int nsteps, double dt, int m,
                                   double tol, const double* A_xy_host, dirac_step_info* info) {
+  dirac::TraceRange trace("dirac_propagate_host");
   if (!ctx) return fail(DIRAC_EINVAL, "null context");
   if (!psi_host) return fail(DIRAC_EINVAL, "null psi");
   Engine& e = ctx->e;
@@ -1066,6 +1068,7 @@ dirac_status dirac_batch_set_launch_shape(dirac_batch* bt, int tile_height, int 
 
 dirac_status dirac_batch_steps(dirac_batch* bt, void* const* psi_dev, int nsteps, double dt, int m,
                                double tol, const double* A_xy_host, dirac_step_info* info) {
+  dirac::TraceRange trace("dirac_batch_steps");
   if (!bt) return fail(DIRAC_EINVAL, "null batch");
   if (!psi_dev) return fail(DIRAC_EINVAL, "null psi table");
   dirac_status s = bt->e.run(reinterpret_cast<vec4* const*>(psi_dev), nsteps, dt, m, tol, A_xy_host);

@@ -873,6 +873,7 @@ dirac_status dirac_lanczos_eigs(dirac_ctx* ctx, const void* start_dev, int n_wan
                                 int check_every, double tol, double e_lo, double e_hi, int reorth,
                                 int fold, double sigma, double* eigs_out, double* bounds_out,
                                 void* vecs_dev, dirac_eig_info* info) {
+  dirac::TraceRange trace("dirac_lanczos_eigs");
   CtxView v;
   dirac_status st = ctx_view(ctx, &v);
   if (st != DIRAC_OK) return st;

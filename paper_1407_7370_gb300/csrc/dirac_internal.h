@@ -6,8 +6,18 @@
 #include "dirac.h"
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 namespace dirac {
+
+// NVTX range around a public call, so that timeline tools show the library's
+// calls; without a tool attached the push and pop do nothing.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // Records a printf-style message for dirac_last_error() and returns `s`.
 dirac_status fail(dirac_status s, const char* fmt, ...);
