@@ -196,3 +196,46 @@ def test_batch_256_full_size_sampled(precision):
         err = lz.rel_l2(psis[k].cpu().numpy(), ref)
         tol = fp64_tol(steps, dt) if precision == "fp64" else mixed_tol(steps, dt, hnorm(g, A[:steps, k]))
         assert err <= tol, (k, g.nx, err, tol)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_per_problem_stopping(precision):
+    """Problems of one batch stop at their own Krylov dimension: an exact
+    plane-wave eigenvector breaks down after one iteration (FP64), the zero
+    state is a trivial step, and with tol > 0 a slow and a fast packet stop
+    at different k (Eq. 18) -- each as the oracle run alone does."""
+    from paper_1407_7370_gb300 import BatchPropagator
+    from tests.test_oracle_hamiltonian import plane_wave_eigpair
+    grids = [wl.Grid(32, 24, 0.1, 0.1), wl.Grid(48, 40, 0.1, 0.1), wl.Grid(40, 40, 0.05, 0.05),
+             wl.Grid(17, 9, 0.1, 0.1)]
+    pw, _ = plane_wave_eigpair(32, 24, 0.1, 0.1, 2, 1, 2, (0.0, 0.0), 0.0)
+    states = [pw, wl.positive_energy_packet(grids[1], p0=(0.5, 0.0), sigma_x=2.0),
+              wl.positive_energy_packet(grids[2], p0=(40.0, 10.0), sigma_x=0.3),
+              np.zeros((9, 17, 2), complex)]
+    dt, m, tol, steps = 2e-4, 16, 1e-9, 2
+    shift = 137.036 ** 2 if precision == "mixed" else 0.0
+    bp = BatchPropagator([(g.nx, g.ny, g.dx, g.dy) for g in grids], m_max=m, precision=precision)
+    for k in range(len(grids)):
+        bp.set_fields(k, shift=shift)
+    psis = [torch.from_numpy(s.copy()).cuda() for s in states]
+    infos = bp.steps(psis, steps, dt, m, tol=tol, info=True)
+    assert not np.any(psis[3].cpu().numpy()) and infos[3].k_used == 1
+    if precision == "fp64":   # FP32 stencil rounding leaves beta_1 ~ u32 ||H||: no exact breakdown
+        assert infos[0].k_used == 1 and infos[0].breakdown
+    ks = []
+    for k in range(3):
+        g = grids[k]
+        op = ham.Operator(g.nx, g.ny, g.dx, g.dy, shift=shift)
+        ref = states[k].copy()
+        for _ in range(steps):
+            ref, oi = lz.krylov_step(op, ref, dt, m, tol=tol)
+        out = psis[k].cpu().numpy()
+        if precision == "fp64":
+            assert infos[k].k_used == oi.k_used, (k, infos[k].k_used, oi.k_used)
+            assert lz.rel_l2(out, ref) <= fp64_tol(steps, dt)
+        else:
+            if k > 0:
+                assert abs(infos[k].k_used - oi.k_used) <= 1
+            assert lz.rel_l2(out, ref) <= mixed_tol(steps, dt, hnorm(g, np.zeros((1, 2))))
+        ks.append(infos[k].k_used)
+    assert ks[1] < ks[2]      # the fast, narrow packet needs a larger Krylov space
