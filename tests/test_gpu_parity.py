@@ -360,6 +360,35 @@ def test_degenerate_thin_grids(nx, ny, order, boundary):
         assert lz.rel_l2(out, ref) <= fp64_tol(3, 1e-3)
 
 
+@pytest.mark.parametrize("precision,mode", [("fp64", "one_launch"), ("fp64", "passes"),
+                                            ("mixed", "passes")])
+def test_backward_steps(precision, mode):
+    """dt < 0: psi <- exp(+i H |dt|) psi, against the oracle (the dense
+    exponential pins the oracle's backward step); a forward run followed by
+    the backward run with the fields in reverse order returns to psi_0."""
+    g = wl.Grid(40, 32, 0.1, 0.1)
+    psi0 = wl.positive_energy_packet(g, p0=(6.0, 2.0))
+    V = wl.soft_core(g, 1.0)
+    rng = np.random.default_rng(8)
+    A = rng.uniform(-5, 5, size=(4, 2))
+    shift = C * C if precision == "mixed" else 0.0
+    back, _, _ = gpu_run(g, psi0, -1e-4, 12, 4, V=V, A_steps=A, precision=precision, step_mode=mode,
+                         shift=shift)
+    op = oracle_op(g, V=V, shift=shift)
+    ref = psi0.copy()
+    for s in range(4):
+        op.A = tuple(A[s])
+        ref, _ = lz.krylov_step(op, ref, -1e-4, 12)
+    hn = max(hnorm(g, tuple(a), V) for a in A)
+    tol = fp64_tol(4, 1e-4) if precision == "fp64" else mixed_tol(4, 1e-4, hn)
+    assert lz.rel_l2(back, ref) <= tol
+    fwd, _, _ = gpu_run(g, psi0, 1e-4, 12, 4, V=V, A_steps=A, precision=precision, step_mode=mode,
+                        shift=shift)
+    ret, _, _ = gpu_run(g, fwd, -1e-4, 12, 4, V=V, A_steps=A[::-1].copy(), precision=precision,
+                        step_mode=mode, shift=shift)
+    assert lz.rel_l2(ret, psi0) <= 2 * tol
+
+
 def test_one_launch_barrier_timeout_is_reported_and_the_context_recovers():
     """Every grid-barrier wait of the one-launch step is bounded: a step whose
     barriers wait for one CTA more than the launch has ends with DIRAC_ECUDA

@@ -76,6 +76,19 @@ def test_step_matches_dense_expm(order, boundary):
     assert err8 > 1e-14 and info8.err_est >= 0.1 * err8 and info8.err_est <= 1e3 * err8
 
 
+@pytest.mark.parametrize("shift", [0.0, 137.036 ** 2])
+def test_backward_step_matches_dense_expm(shift):
+    """dt < 0 (the adjoint's backward propagation): exp(+i H |dt|) psi."""
+    g, op = _tiny_op(4, ham.DIRICHLET)
+    op.shift = shift
+    psi = wl.random_spinor(g, 14)
+    dt = -1e-4
+    h = ham.dense(op) + shift * np.eye(2 * g.nx * g.ny)     # H itself: the shift only changes a phase
+    ref = (scipy.linalg.expm(-1j * dt * h) @ psi.reshape(-1)).reshape(psi.shape)
+    out, info = lz.krylov_step(op, psi, dt, m=30)
+    assert lz.rel_l2(out, ref) <= 1e-12
+
+
 def test_step_with_shift_equals_unshifted():
     g, op = _tiny_op()
     psi = wl.random_spinor(g, 13)
