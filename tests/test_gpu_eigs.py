@@ -309,3 +309,19 @@ def test_full_reorthogonalisation_has_no_ghost_eigenvalues():
         j = min(free_idx, key=lambda k: abs(exact[k] - v))
         assert abs(exact[j] - v) <= tol, (v, exact[j])
         used.add(j)
+
+
+@pytest.mark.parametrize("order,boundary", [(4, "dirichlet"), (4, "periodic"), (2, "dirichlet")])
+def test_eigs_other_stencils_and_a_field_match_oracle(order, boundary):
+    """The eigen mode with the fourth-order stencil, Dirichlet boundaries and
+    a uniform vector potential (both components): Ritz values, iteration
+    count and convergence as the oracle."""
+    g, V, start = soft_core_case(22, 18, 0.3, 2.0)
+    A = (5.0, -2.0)
+    p, op = make(g, V=V, A=A, shift=C * C, order=order, boundary=boundary)
+    window = (-C * C, 0.0)
+    res = p.eigs(dev(start), n_want=8, max_iter=400, tol=1e-9, window=window, check_every=10)
+    ref = lz.lanczos_eigs(op, start, n_want=8, max_iter=400, tol=1e-9, window=window, check_every=10)
+    assert res.iterations == ref.iterations
+    assert res.values.size == ref.values.size >= 2
+    assert np.max(np.abs(res.values - ref.values)) <= 1e-11 * norm_a(op)
