@@ -453,11 +453,13 @@ template <class S, int R, int TH>
 __host__ __device__ constexpr size_t worker_bytes() { return tile_bytes<S, R, TH>() + qbuf_bytes<S, R, TH>(); }
 
 // tile workers per CTA of the one-launch step: one CTA per SM on both paths
-// (two workers of eight warps on FP64; 1024 threads of 128-thread workers on
-// FP32), so that a grid barrier and its partial sums involve one CTA per SM
+// (two workers of eight warps on FP64; 768 threads on FP32 -- six 128-thread
+// or three 256-thread workers, 80 registers each, where 1024 threads at 64
+// registers spilled), so that a grid barrier and its partial sums involve one
+// CTA per SM
 template <class S, int TH>
 __host__ __device__ constexpr int step_workers() {
-  return sizeof(S) == sizeof(double) ? 2 : 1024 / (32 * (TH / 4));
+  return sizeof(S) == sizeof(double) ? 2 : 768 / (32 * (TH / 4));
 }
 
 // Chunks of the tile list: CTA c takes q + 1 tiles if c < r, else q (q = T / G,
