@@ -54,8 +54,8 @@ def STEP_BYTES_PER_SITE_MIXED(m):    # complex64 basis; psi read and written in 
 # DRAM traffic per launch from the last ncu capture of each kernel on the
 # configured grid, valid only for the kernel source it was taken with (sha1 of
 # dirac_kernels.cuh).
-TRAFFIC = {"lanczos_step<double>": ("2adaa393ff12", 1.635619e9 + 1.302793e9),
-           "lanczos_pass<float>": ("2adaa393ff12", 33.624320e6 + 0.664832e6)}
+TRAFFIC = {"lanczos_step<double>": ("fdb569ea81c3", 1.638726e9 + 1.302841e9),
+           "lanczos_pass<float>": ("fdb569ea81c3", 33.633280e6 + 0.583680e6)}
 
 
 def kernel_sha() -> str:
