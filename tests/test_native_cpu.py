@@ -1,6 +1,7 @@
 """CPU-side checks of the C ABI: the library builds, loads, exports every
 function that include/dirac.h declares, and its host-only pieces behave."""
 import ctypes
+import os
 
 import pytest
 
@@ -95,3 +96,25 @@ def test_no_gpu_gives_cuda_error_not_a_crash(lib):
     st = lib.dirac_create(ctypes.byref(ctx), 8, 8, 0.1, 0.1, 1.0, 137.036, 2, 0, 0, 4, None)
     assert st in (nat.ECUDA, nat.ENOMEM)
     assert not ctx.value
+
+
+def test_c99_client_compiles_links_and_runs(tmp_path, lib):
+    """include/dirac.h is a C header: a C99 program (tests/c/abi_check.c)
+    compiles against it with warnings as errors, links the library and gets
+    the documented results from the calls that need no GPU."""
+    import shutil
+    import subprocess
+    from paper_1407_7370_gb300 import build
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    here = os.path.dirname(os.path.abspath(__file__))
+    so_dir = os.path.dirname(build.LIB)
+    exe = str(tmp_path / "abi_check")
+    cmd = [gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+           "-I", os.path.join(build.ROOT, "include"), os.path.join(here, "c", "abi_check.c"),
+           "-o", exe, "-L", so_dir, "-ldirac_gb300", "-Wl,-rpath," + so_dir, "-lm"]
+    res = subprocess.run(cmd, capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr
+    run = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert run.returncode == 0 and "abi_check ok" in run.stdout, run.stdout + run.stderr
