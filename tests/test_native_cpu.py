@@ -118,3 +118,34 @@ def test_c99_client_compiles_links_and_runs(tmp_path, lib):
     assert res.returncode == 0, res.stderr
     run = subprocess.run([exe], capture_output=True, text=True, timeout=60)
     assert run.returncode == 0 and "abi_check ok" in run.stdout, run.stdout + run.stderr
+
+
+@pytest.mark.gpu
+def test_c99_client_propagates_on_the_gpu(tmp_path):
+    """tests/c/propagate_check.c: device memory from the CUDA runtime, ten
+    FP64 steps through the C ABI, unitary to 1e-12."""
+    import shutil
+    import subprocess
+    from paper_1407_7370_gb300 import build
+    build.build()
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    cuda = os.path.dirname(os.path.dirname(build.nvcc_path()))
+    lib64 = next((p for p in (os.path.join(cuda, "lib64"), os.path.join(cuda, "lib"),
+                              os.path.join(cuda, "targets", "sbsa-linux", "lib"),
+                              os.path.join(cuda, "targets", "x86_64-linux", "lib"))
+                  if os.path.exists(os.path.join(p, "libcudart.so"))), None)
+    if lib64 is None:
+        pytest.fail("libcudart.so not found under " + cuda)
+    here = os.path.dirname(os.path.abspath(__file__))
+    so_dir = os.path.dirname(build.LIB)
+    exe = str(tmp_path / "propagate_check")
+    cmd = [gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(build.ROOT, "include"),
+           "-I", os.path.join(cuda, "include"), os.path.join(here, "c", "propagate_check.c"), "-o", exe,
+           "-L", so_dir, "-ldirac_gb300", "-Wl,-rpath," + so_dir, "-L", lib64, "-lcudart",
+           "-Wl,-rpath," + lib64, "-lm"]
+    res = subprocess.run(cmd, capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr
+    run = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert run.returncode == 0 and "propagate_check ok" in run.stdout, run.stdout + run.stderr
