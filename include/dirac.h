@@ -316,16 +316,20 @@ long long dirac_batch_kernel_launches(const dirac_batch* batch);
  * calling cudaMalloc, a memory budget fixed up front, or a per-step loop in
  * which an allocation's latency or failure is not acceptable.
  *
- * It performs one time step, in place on psi_dev, exactly as
- * dirac_lanczos_step would for a context created with the same problem
- * (dirac_problem below), but keeps its whole workspace in one static device
- * array of dirac_noalloc_scratch_bytes() bytes (8 MiB) per device, and calls
- * no cudaMalloc, cudaFree or other allocating routine.  Problems whose
+ * It performs one FP64 time step, in place on psi_dev, as dirac_lanczos_step
+ * would for an FP64 context created with the same problem (dirac_problem
+ * below) and launched one pass at a time, dt < 0 stepping backwards as
+ * there, but keeps its whole workspace in one static device array of
+ * dirac_noalloc_scratch_bytes() bytes (8 MiB) per device, and calls no
+ * cudaMalloc, cudaFree or other allocating routine.  Problems whose
  * workspace, about (m + 1) * nx * ny * 32 bytes, does not fit are rejected
- * with DIRAC_EINVAL.
+ * with DIRAC_EINVAL.  The per-call tables reach the device as kernel
+ * arguments; no host buffer is read after the call returns.
  *  - The first call on each device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *    (cudaGetSymbolAddress) with that device current and keeps it for the
+ *    life of the process; make that first call before any stream capture.
+ *    cudaDeviceReset unloads the array: do not call this entry point on a
+ *    device after resetting it.
  *  - Every call in the process shares the one array, and the array keeps the
  *    previous call's contents (the call clears what must start at zero).
  *    Calls whose work overlaps on the GPU -- on different streams, or from
@@ -336,6 +340,11 @@ long long dirac_batch_kernel_launches(const dirac_batch* batch);
  *    (DIRAC_ENONFINITE) are only reported when info is requested.
  * psi_dev, V_dev: device buffers owned by the caller, laid out as for
  * dirac_lanczos_step / dirac_set_fields.  cuda_stream: a cudaStream_t.
+ * Errors: DIRAC_EINVAL (the problem's sizes, spacings, order, boundary or
+ * scalars as for dirac_create / dirac_set_fields; m outside
+ * 1..DIRAC_KRYLOV_MAX; dt = 0 or non-finite; tol < 0; misaligned psi; a
+ * workspace beyond the scratch; V with non-finite entries), DIRAC_ENONFINITE
+ * (only with info), DIRAC_ECUDA.
  */
 typedef struct {
     int nx, ny;
@@ -498,6 +507,21 @@ dirac_status dirac_adjoint_gradient(dirac_ctx* ctx, const void* psi0_dev, int ns
                                     const double* A_xy_host, const dirac_adjoint_opts* opts,
                                     double* loss_out, void* psiN_dev, void* dV_dev, double* dA_host,
                                     double* da_host, dirac_adjoint_info* info);
+
+/*
+ * Measured arithmetic peak of the current GPU, the denominator of the
+ * roofline of the kernels that are bound by arithmetic rather than memory
+ * (the FP64 path).  The paper has no counterpart: it is a measurement
+ * utility.  kind DIRAC_PEAK_FP64 or DIRAC_PEAK_FP32: every SM's resident
+ * threads run eight independent fused multiply-add chains each; *tflops
+ * receives 2 x (FMAs) / (best CUDA-event time of three launches after one
+ * warm-up), in TFLOP/s.  Runs on a private stream, allocates a few bytes,
+ * synchronises; takes about a quarter of a second.
+ * Errors: DIRAC_EINVAL (kind, null output), DIRAC_ECUDA.
+ */
+#define DIRAC_PEAK_FP64 0
+#define DIRAC_PEAK_FP32 1
+dirac_status dirac_measure_peak(int kind, double* tflops);
 
 /*
  * Test hook for the device small-matrix exponential: v = exp(-i T dt) e_1 for

@@ -24,6 +24,7 @@ PERIODIC, DIRICHLET = 0, 1
 FP64, MIXED = 0, 1
 OBS_PX, OBS_PROJ = 0, 1
 STEP_AUTO, STEP_PASSES, STEP_ONE_LAUNCH = 0, 1, 2
+PEAK_FP64, PEAK_FP32 = 0, 1
 
 
 class StepInfoC(ctypes.Structure):
@@ -112,6 +113,7 @@ def lib():
         "dirac_status_string": (ctypes.c_char_p, [i]),
         "dirac_last_error": (ctypes.c_char_p, []),
         "dirac_debug_tridiag_expm": (i, [dp, dp, i, d, d, d, dp, dp]),
+        "dirac_measure_peak": (i, [i, dp]),
         "dirac_profile_enable": (i, [vp, i]),
         "dirac_lanczos_step_noalloc": (i, [ctypes.POINTER(ProblemC), vp, d, i, d, vp,
                                            ctypes.POINTER(StepInfoC)]),

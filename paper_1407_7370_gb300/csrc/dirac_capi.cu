@@ -160,20 +160,13 @@ struct LaunchShape {
 // from the others' by at most one tile.
 template <class S, int R, int TH, bool D, bool V, bool AY>
 cudaError_t launch_pass_t(LaunchParams p, const LaunchShape& ls, cudaStream_t s) {
-  static int occ = 0;
+  static std::atomic<int> occ_dev[OCC_MAX_DEVICES];
   constexpr int NT = sub_workers<S>() * 32 * (TH / rows_per_thread<S, TH>());
   constexpr size_t smem = dyn_smem_bytes<S, R, TH, sub_workers<S>()>();
-  if (occ == 0) {
-    cudaError_t e = cudaSuccess;
-    if (smem > 0) {
-      e = cudaFuncSetAttribute(lanczos_pass<S, R, TH, D, V, AY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
-      if (e != cudaSuccess) return e;
-    }
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lanczos_pass<S, R, TH, D, V, AY>, NT, smem);
-    if (e != cudaSuccess) return e;
-    if (occ < 1) occ = 1;
-  }
+  int occ = 0;
+  cudaError_t e = occupancy_on_device(occ_dev, lanczos_pass<S, R, TH, D, V, AY>, NT, smem, &occ);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) occ = 1;
   const int per_sm = ls.cta_cap > 0 ? std::min(occ, ls.cta_cap) : occ;
   const int slots = std::max(1, ls.n_sm * per_sm);
   const int grid = std::max(1, std::min(p.total_tiles, slots));
@@ -846,6 +839,69 @@ dirac_status cheb_params(double c0, double half, double dt, double shift, ChebPa
 
 }  // namespace dirac
 
+namespace {
+
+// ----------------------------- measured peak -------------------------------
+
+// Independent fused multiply-add chains, eight per thread, iterated to a
+// bounded fixed point (x -> a x + b with |a| < 1): no overflow, no
+// subnormals, and a result the compiler cannot drop.
+template <class T>
+__global__ void __launch_bounds__(256) fma_peak_kernel(T* sink, int iters, T a, T b) {
+  constexpr int C = 8;
+  T x[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) x[c] = (T)(threadIdx.x + c);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) x[c] = fma(x[c], a, b);
+  }
+  T t = (T)0;
+#pragma unroll
+  for (int c = 0; c < C; ++c) t += x[c];
+  if (t == (T)-1.0) sink[blockIdx.x] = t;   // never true: keeps the chains live
+}
+
+template <class T>
+dirac_status measure_fma_peak(int iters, double* tflops) {
+  int dev = 0, n_sm = 0, occ = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fma_peak_kernel<T>, 256, 0));
+  const int grid = n_sm * std::max(occ, 1);
+  T* sink = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaStream_t st = nullptr;
+  CUDA_TRY(cudaMalloc(&sink, sizeof(T) * grid));
+  cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const T a = (T)(1.0 - 1.0 / 1048576.0), b = (T)(1.0 / 1024.0);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {   // the first run warms up
+    e = cudaEventRecord(e0, st);
+    if (e == cudaSuccess) {
+      fma_peak_kernel<T><<<grid, 256, 0, st>>>(sink, iters, a, b);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && rep > 0) best = std::min(best, ms);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) cudaStreamDestroy(st);
+  cudaFree(sink);
+  if (e != cudaSuccess) return fail(DIRAC_ECUDA, "peak measurement: %s", cudaGetErrorString(e));
+  const double fmas = (double)grid * 256.0 * 8.0 * (double)iters;
+  *tflops = 2.0 * fmas / (best * 1e-3) / 1e12;
+  return DIRAC_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* dirac_status_string(dirac_status s) {
@@ -1244,6 +1300,14 @@ dirac_status dirac_batch_autotune(dirac_batch* bt, void* const* psi_dev, double 
 
 // ----------------------------- test hook -----------------------------------
 
+dirac_status dirac_measure_peak(int kind, double* tflops) {
+  if (!tflops) return fail(DIRAC_EINVAL, "null output");
+  // about 50 ms per launch on a GB300 at full clock
+  if (kind == DIRAC_PEAK_FP64) return measure_fma_peak<double>(12000, tflops);
+  if (kind == DIRAC_PEAK_FP32) return measure_fma_peak<float>(600000, tflops);
+  return fail(DIRAC_EINVAL, "unknown peak kind %d", kind);
+}
+
 dirac_status dirac_debug_tridiag_expm(const double* alpha, const double* beta, int k, double dt,
                                       double lo, double hi, double* v_re, double* v_im) {
   if (k < 1 || k > DIRAC_KRYLOV_MAX) return fail(DIRAC_EINVAL, "k outside 1..%d", DIRAC_KRYLOV_MAX);
@@ -1293,7 +1357,10 @@ std::atomic<void*> g_noalloc_ptr[NOALLOC_MAX_DEVICES];
 
 // Device address of the scratch array on the current device.  In host code
 // `g_noalloc_scratch` names a host-side shadow, not device memory, so the
-// address is looked up once per device (with that device current).
+// address is looked up once per device (with that device current) and kept
+// for the life of the process.  cudaDeviceReset unloads the module; the kept
+// address is then stale, so a process that resets a device must not call the
+// allocation-free step on it again.
 dirac_status noalloc_scratch(unsigned char** out) {
   int dev = 0;
   CUDA_TRY(cudaGetDevice(&dev));
@@ -1305,6 +1372,30 @@ dirac_status noalloc_scratch(unsigned char** out) {
   }
   *out = static_cast<unsigned char*>(p);
   return DIRAC_OK;
+}
+
+// The per-call tables travel as kernel arguments (no host buffer is read
+// after the call returns): one CTA writes them into the scratch and clears
+// the step counter, the block map (every block is problem 0) and the scalar
+// block, which the scratch keeps from the previous call.
+struct NoallocTables {
+  Problem pr;
+  ChebParams cheb;
+  FieldStep fs;
+};
+
+__global__ void noalloc_setup(const __grid_constant__ NoallocTables t, Problem* pr, ChebParams* cheb,
+                              FieldStep* fs, int* step_and_blocks, int n_words, DevState* st) {
+  if (threadIdx.x == 0) {
+    *pr = t.pr;
+    *fs = t.fs;
+  }
+  const double* src = reinterpret_cast<const double*>(&t.cheb);
+  double* dst = reinterpret_cast<double*>(cheb);
+  for (int w = threadIdx.x; w < (int)(sizeof(ChebParams) / sizeof(double)); w += blockDim.x) dst[w] = src[w];
+  for (int w = threadIdx.x; w < n_words; w += blockDim.x) step_and_blocks[w] = 0;
+  unsigned* sw = reinterpret_cast<unsigned*>(st);
+  for (int w = threadIdx.x; w < (int)(sizeof(DevState) / sizeof(unsigned)); w += blockDim.x) sw[w] = 0u;
 }
 
 }  // namespace
@@ -1320,7 +1411,9 @@ extern "C" dirac_status dirac_lanczos_step_noalloc(const dirac_problem* pb, void
   if (s != DIRAC_OK) return s;
   if (!std::isfinite(pb->A_x) || !std::isfinite(pb->A_y) || !std::isfinite(pb->energy_shift))
     return fail(DIRAC_EINVAL, "non-finite field scalar");
-  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(DIRAC_EINVAL, "dt must be finite and > 0");
+  if (!(dt != 0.0) || !std::isfinite(dt)) return fail(DIRAC_EINVAL, "dt must be finite and nonzero");
+  const bool backward = dt < 0.0;   // exp(+i H |dt|): the conjugate of the forward coefficients
+  dt = std::fabs(dt);
   if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(DIRAC_EINVAL, "tol must be finite and >= 0");
   if (!aligned32(psi_dev)) return fail(DIRAC_EINVAL, "psi must be 32-byte aligned");
 
@@ -1368,11 +1461,8 @@ extern "C" dirac_status dirac_lanczos_step_noalloc(const dirac_problem* pb, void
     vmin = h[0];
     vmax = h[1];
   }
-  struct {
-    Problem pr;
-    ChebParams cheb;
-    FieldStep fs;
-  } host;   // on the stack; copied into the scratch
+  static_assert(sizeof(ChebParams) % sizeof(double) == 0, "ChebParams copied as doubles");
+  NoallocTables host;   // passed by value to the setup kernel
   std::memset(&host, 0, sizeof(host));
   double c0, half;
   spectral_interval(pb->stencil_order, pb->dx, pb->dy, pb->mass, pb->c, std::fabs(pb->A_x),
@@ -1403,13 +1493,10 @@ extern "C" dirac_status dirac_lanczos_step_noalloc(const dirac_problem* pb, void
   host.fs.cAy = pb->c * pb->A_y;
   host.fs.cAxf = (float)host.fs.cAx;
   host.fs.cAyf = (float)host.fs.cAy;
-  CUDA_TRY(cudaMemcpyAsync(base, &host.pr, sizeof(Problem), cudaMemcpyHostToDevice, stream));
-  CUDA_TRY(cudaMemcpyAsync(base + off_cheb, &host.cheb, sizeof(ChebParams), cudaMemcpyHostToDevice, stream));
-  CUDA_TRY(cudaMemcpyAsync(base + off_field, &host.fs, sizeof(FieldStep), cudaMemcpyHostToDevice, stream));
-  // the scratch keeps the previous call's contents: restart the step counter,
-  // the block map (every block is problem 0) and the scalar block
-  CUDA_TRY(cudaMemsetAsync(step, 0, sizeof(int) * (1 + RB_MAX), stream));
-  CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(DevState), stream));
+  noalloc_setup<<<1, 256, 0, stream>>>(host, reinterpret_cast<Problem*>(base),
+                                       reinterpret_cast<ChebParams*>(base + off_cheb),
+                                       reinterpret_cast<FieldStep*>(base + off_field), step, 1 + RB_MAX, st);
+  CUDA_TRY(cudaGetLastError());
 
   LaunchParams lp;
   std::memset(&lp, 0, sizeof(lp));
@@ -1423,6 +1510,7 @@ extern "C" dirac_status dirac_lanczos_step_noalloc(const dirac_problem* pb, void
   lp.m = m;
   lp.mcc = mcc;
   lp.dt = dt;
+  lp.conj_coef = backward ? 1 : 0;
   lp.tol = tol;
   lp.step = step;
   lp.redo_budget = redo_budget(DIRAC_FP64, m);

@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
+#include <atomic>
+
 namespace dirac {
 
 // NVTX range around a public call, so that timeline tools show the library's
@@ -46,6 +48,33 @@ dirac_status ctx_view(dirac_ctx* ctx, CtxView* v);
 struct ChebParams;
 struct LaunchParams;
 struct CoopArgs;
+
+// Resident CTAs per SM of `kernel` (threads, dynamic shared memory smem) on
+// the current device.  Computed once per device -- after raising the
+// kernel's dynamic shared memory limit there -- and kept in cache[device],
+// an array of OCC_MAX_DEVICES zero-initialised entries that the caller
+// declares once per kernel.  Threads may race on the first call: each
+// computes the same value.
+constexpr int OCC_MAX_DEVICES = 64;
+template <class Kernel>
+cudaError_t occupancy_on_device(std::atomic<int>* cache, Kernel kernel, int threads, size_t smem, int* occ) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= OCC_MAX_DEVICES) return cudaErrorInvalidDevice;
+  int v = cache[dev].load(std::memory_order_acquire);
+  if (v == 0) {
+    if (smem > 0) {
+      e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (v > 0) cache[dev].store(v, std::memory_order_release);
+  }
+  *occ = v;
+  return cudaSuccess;
+}
 
 // FP32 passes stage their tiles by asynchronous copies from this many tiles
 // per CTA on (below that the extra barrier costs more than it hides)

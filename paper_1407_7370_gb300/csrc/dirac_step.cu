@@ -17,21 +17,14 @@ namespace {
 
 template <class S, int R, int TH, bool D, bool V, bool AY>
 cudaError_t launch_step_t(LaunchParams p, int n_sm, CoopArgs ca, cudaStream_t s) {
-  static int occ = 0;
+  static std::atomic<int> occ_dev[OCC_MAX_DEVICES];
   constexpr int SUB = step_workers<S, TH>();
   constexpr int NT = SUB * 32 * (TH / rows_per_thread<S, TH>());
   constexpr size_t smem = dyn_smem_bytes<S, R, TH, SUB>();
-  if (occ == 0) {
-    cudaError_t e = cudaSuccess;
-    if (smem > 0) {
-      e = cudaFuncSetAttribute(lanczos_step<S, R, TH, D, V, AY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
-      if (e != cudaSuccess) return e;
-    }
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lanczos_step<S, R, TH, D, V, AY>, NT, smem);
-    if (e != cudaSuccess) return e;
-    if (occ < 1) return cudaErrorCooperativeLaunchTooLarge;
-  }
+  int occ = 0;
+  cudaError_t e = occupancy_on_device(occ_dev, lanczos_step<S, R, TH, D, V, AY>, NT, smem, &occ);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) return cudaErrorCooperativeLaunchTooLarge;
   // every CTA resident (a cooperative launch checks it) and each with at
   // least one tile, so that every CTA writes its partial in every pass
   const int grid = std::max(1, std::min(std::min(p.total_tiles, n_sm * occ), ca.cap));
