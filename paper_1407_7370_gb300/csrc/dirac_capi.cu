@@ -222,9 +222,14 @@ cudaError_t launch_recombine(int precision, const RecombParams& rp, int grid, cu
   return launch_pdl(recombine<true>, grid, 256, 0, s, rp);
 }
 
-__global__ void to_float_kernel(const double* in, float* out, long long n) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    out[i] = (float)in[i];
+// FP64 -> FP32 pair: hi = (float)v, lo = (float)(v - hi)
+__global__ void split_float_kernel(const double* in, float* hi, float* lo, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = in[i];
+    const float h = (float)v;
+    hi[i] = h;
+    lo[i] = (float)(v - (double)h);
+  }
 }
 
 __global__ void minmax_kernel(const double* v, long long n, double* out) {
@@ -266,6 +271,7 @@ struct HostProblem {
   void* basis = nullptr;
   void* ybuf[2] = {nullptr, nullptr};
   void* V = nullptr;               // double (FP64) or float (mixed) copy
+  float* Vlo = nullptr;            // mixed: V - (float)V
   double* V64 = nullptr;           // double copy (== V on the FP64 path)
   bool has_v = false;
   double vmin = 0, vmax = 0;
@@ -314,11 +320,14 @@ struct Engine {
   size_t ev_used = 0;
 
   int nprob() const { return (int)P.size(); }
+  // FP64, one problem: one cooperative launch per step (lanczos_step)
   bool use_step_kernel(int np) const {
-    if (np != 1 || !d_coop_slots) return false;
-    if (step_mode == DIRAC_STEP_AUTO) return precision == DIRAC_FP64;
-    return step_mode == DIRAC_STEP_ONE_LAUNCH;
+    if (np != 1 || !d_coop_slots || precision != DIRAC_FP64) return false;
+    return step_mode == DIRAC_STEP_AUTO || step_mode == DIRAC_STEP_ONE_LAUNCH;
   }
+  // mixed precision, any number of problems: one cooperative launch per step
+  // (lanczos_step_m32) unless per-pass launches are asked for
+  bool use_m32() const { return precision == DIRAC_MIXED && step_mode != DIRAC_STEP_PASSES; }
   cudaError_t mark(int kind);
   dirac_status init(int n, const int* nx, const int* ny, const double* dx, const double* dy, double mass_,
                     double c_, int order_, int boundary_, int precision_, int m_max_, void* stream_);
@@ -425,8 +434,8 @@ dirac_status Engine::init(int n, const int* nx, const int* ny, const double* dx,
   if (n == 1) {
     coop_cap = shape.n_sm * 8;     // the most resident CTAs of any pass kernel
     CUDA_TRY(cudaMalloc(&d_coop_slots, 2 * 3 * sizeof(double) * coop_cap));
-    CUDA_TRY(cudaMalloc(&d_coop_bar, GRID_SYNC_WORDS * sizeof(unsigned)));
   }
+  CUDA_TRY(cudaMalloc(&d_coop_bar, GRID_SYNC_WORDS * sizeof(unsigned)));
   CUDA_TRY(cudaMemsetAsync(d_st, 0, sizeof(DevState) * n, stream));
   CUDA_TRY(cudaEventCreateWithFlags(&tab_ev, cudaEventDisableTiming));
   // recombination blocks in proportion to the problem sizes
@@ -458,6 +467,7 @@ void Engine::release() {
   for (HostProblem& q : P) {
     if (q.V64 != q.V) cudaFree(q.V64);
     cudaFree(q.V);
+    cudaFree(q.Vlo);
   }
   cudaFree(d_st);
   cudaFreeHost(h_st);
@@ -493,7 +503,8 @@ dirac_status Engine::set_fields(int b, const double* V_dev, double ax, double ay
     const bool f32 = precision != DIRAC_FP64;
     if (!q.V) CUDA_TRY(cudaMalloc(&q.V, (f32 ? sizeof(float) : sizeof(double)) * q.n));
     if (f32) {
-      to_float_kernel<<<256, 256, 0, stream>>>(V_dev, static_cast<float*>(q.V), q.n);
+      if (!q.Vlo) CUDA_TRY(cudaMalloc(&q.Vlo, sizeof(float) * q.n));
+      split_float_kernel<<<256, 256, 0, stream>>>(V_dev, static_cast<float*>(q.V), q.Vlo, q.n);
       ++launches;
       CUDA_TRY(cudaGetLastError());
       if (!q.V64) CUDA_TRY(cudaMalloc(&q.V64, sizeof(double) * q.n));
@@ -540,7 +551,9 @@ dirac_status Engine::run(vec4* const* psi, int nsteps, double dt, int m, double 
   if (a_xy)
     for (long long k = 0; k < 2LL * nsteps * np; ++k)
       if (!std::isfinite(a_xy[k])) return fail(DIRAC_EINVAL, "non-finite vector potential in the schedule");
-  const int th = shape.th ? shape.th : (precision == DIRAC_FP64 ? fp64_tile_height(P, shape.n_sm) : 16);
+  const bool m32 = use_m32();
+  const int th = m32 ? M32_TILE_H
+                     : (shape.th ? shape.th : (precision == DIRAC_FP64 ? fp64_tile_height(P, shape.n_sm) : 16));
   // tile list for this tile height
   int tt = 0;
   for (HostProblem& q : P) {
@@ -597,6 +610,7 @@ dirac_status Engine::run(vec4* const* psi, int nsteps, double dt, int m, double 
     d.psi = psi[b];
     d.basis = q.basis; d.ybuf0 = q.ybuf[0]; d.ybuf1 = q.ybuf[1];
     d.V = q.has_v ? q.V : nullptr;
+    d.Vlo = q.has_v ? q.Vlo : nullptr;
     d.st = d_st + b;
     d.partials = d_partials + 3 * q.slot_off;
     d.cheb = reinterpret_cast<const ChebParams*>(db + off_cheb) + b;
@@ -604,6 +618,8 @@ dirac_status Engine::run(vec4* const* psi, int nsteps, double dt, int m, double 
     d.ky = c / (kfac * q.dy);
     d.kxf = (float)d.kx;
     d.kyf = (float)d.ky;
+    d.kxf_lo = (float)(d.kx - (double)d.kxf);
+    d.kyf_lo = (float)(d.ky - (double)d.kyf);
     d.shift = q.shift;
     d.probe_coef = make_coef(1.0, 0.0, 0.0, mcc - q.shift, -mcc - q.shift);
     hasv = hasv || q.has_v;
@@ -619,7 +635,8 @@ dirac_status Engine::run(vec4* const* psi, int nsteps, double dt, int m, double 
     f.cAy = c * ay;
     f.cAxf = (float)f.cAx;
     f.cAyf = (float)f.cAy;
-    f.pad0 = f.pad1 = 0.f;
+    f.cAxf_lo = (float)(f.cAx - (double)f.cAxf);
+    f.cAyf_lo = (float)(f.cAy - (double)f.cAyf);
   }
   CUDA_TRY(cudaMemcpyAsync(d_tab, h_tab, bytes, cudaMemcpyHostToDevice, stream));
   CUDA_TRY(cudaEventRecord(tab_ev, stream));
@@ -639,6 +656,7 @@ dirac_status Engine::run(vec4* const* psi, int nsteps, double dt, int m, double 
   lp.dt = dt;
   lp.conj_coef = backward ? 1 : 0;
   lp.has_ay = has_ay ? 1 : 0;
+  lp.diri = boundary == DIRAC_DIRICHLET ? 1 : 0;
   lp.tol = tol;
   lp.step = d_step;
   lp.redo_budget = redo_budget(precision, m);
@@ -681,7 +699,23 @@ dirac_status Engine::run(vec4* const* psi, int nsteps, double dt, int m, double 
   // runs its own next pass; launches with nothing left to do exit at once),
   // then the recombination.  The launches are the same at every step (the
   // fields come from the table through the device step counter).
+  CoopArgs ca32;
+  ca32.slots = d_coop_slots;
+  ca32.bar = d_coop_bar;
+  ca32.G = 0;
+  ca32.cap = coop_cap;
+  ca32.bar_count = barrier_extra;
   auto enqueue_step = [&](cudaStream_t st, bool count) -> dirac_status {
+    if (m32) {   // the whole step in one launch (the barrier words restart at zero)
+      CUDA_TRY(cudaMemsetAsync(d_coop_bar, 0, GRID_SYNC_WORDS * sizeof(unsigned), st));
+      if (count) CUDA_TRY(mark(KIND_STEP));
+      CUDA_TRY(launch_step_m32(order, diri, lp, shape.n_sm, ca32, st));
+      if (count) {
+        ++launches;
+        CUDA_TRY(mark(KIND_END));
+      }
+      return DIRAC_OK;
+    }
     for (int i = 1; i <= m + lp.redo_budget; ++i) {
       lp.pass = i;
       if (count) CUDA_TRY(mark(KIND_PASS));
@@ -705,7 +739,7 @@ dirac_status Engine::run(vec4* const* psi, int nsteps, double dt, int m, double 
     std::memcpy(kp, &lk, sizeof(lk)); kp += sizeof(lk);
     std::memcpy(kp, &rp, sizeof(rp)); kp += sizeof(rp);
     std::memcpy(kp, &ls, sizeof(ls)); kp += sizeof(ls);
-    const int extra[3] = {precision, (int)hasv, rgrid};
+    const int extra[3] = {precision + 2 * (int)m32, (int)hasv, rgrid};
     std::memcpy(kp, extra, sizeof(extra));
     if (!step_graph || key != graph_key) {
       if (!cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
@@ -720,7 +754,7 @@ dirac_status Engine::run(vec4* const* psi, int nsteps, double dt, int m, double 
       cudaGraphDestroy(g);
       if (e != cudaSuccess) { step_graph = nullptr; return fail(DIRAC_ECUDA, "graph instantiate: %s", cudaGetErrorString(e)); }
       graph_key = key;
-      graph_kernels = m + lp.redo_budget + 1;
+      graph_kernels = m32 ? 1 : m + lp.redo_budget + 1;
     }
     for (int s = 0; s < nsteps; ++s) {
       CUDA_TRY(cudaGraphLaunch(step_graph, stream));
@@ -1487,12 +1521,16 @@ extern "C" dirac_status dirac_lanczos_step_noalloc(const dirac_problem* pb, void
   d.ky = pb->c / (kfac * pb->dy);
   d.kxf = (float)d.kx;
   d.kyf = (float)d.ky;
+  d.kxf_lo = (float)(d.kx - (double)d.kxf);
+  d.kyf_lo = (float)(d.ky - (double)d.kyf);
   d.shift = pb->energy_shift;
   d.probe_coef = make_coef(1.0, 0.0, 0.0, mcc - pb->energy_shift, -mcc - pb->energy_shift);
   host.fs.cAx = pb->c * pb->A_x;
   host.fs.cAy = pb->c * pb->A_y;
   host.fs.cAxf = (float)host.fs.cAx;
   host.fs.cAyf = (float)host.fs.cAy;
+  host.fs.cAxf_lo = (float)(host.fs.cAx - (double)host.fs.cAxf);
+  host.fs.cAyf_lo = (float)(host.fs.cAy - (double)host.fs.cAyf);
   noalloc_setup<<<1, 256, 0, stream>>>(host, reinterpret_cast<Problem*>(base),
                                        reinterpret_cast<ChebParams*>(base + off_cheb),
                                        reinterpret_cast<FieldStep*>(base + off_field), step, 1 + RB_MAX, st);

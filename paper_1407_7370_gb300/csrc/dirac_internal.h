@@ -80,6 +80,18 @@ cudaError_t occupancy_on_device(std::atomic<int>* cache, Kernel kernel, int thre
 // per CTA on (below that the extra barrier costs more than it hides)
 constexpr int ASYNC_MIN_TILES = 4;
 
+// Tile height of the mixed-precision one-launch step (tiles of 32 x 16 sites).
+constexpr int M32_TILE_H = 16;
+
+// One mixed-precision time step of every problem in `p` as one cooperative
+// launch (lanczos_step_m32): one CTA per SM, bulk-copy staging, compensated
+// FP32 stencil.  The tile list must use M32_TILE_H; ca.slots holds 2 x 3 x
+// ca.cap doubles (one problem) and ca.bar GRID_SYNC_WORDS zeroed words;
+// ca.bar_count on entry: extra arrivals the barriers wait for (0; 1 only in
+// the test of the barrier timeout).
+cudaError_t launch_step_m32(int order, bool diri, const LaunchParams& p, int n_sm, const CoopArgs& ca,
+                            cudaStream_t s);
+
 // One time step of the single problem in `p` as one cooperative launch
 // (lanczos_step); sets the grid, the chunks and ca.G.  ca.bar_count on entry:
 // arrivals the barriers wait for beyond the launch's CTAs (0; 1 only in the

@@ -106,10 +106,11 @@ struct ChebParams {
   double ci[CHEB_MAX];      //                               imaginary part
 };
 
-// c * A of one step (electron: p - qA = p + A), FP64 and FP32
+// c * A of one step (electron: p - qA = p + A), FP64 and as FP32 pairs
+// (rounded value and remainder)
 struct FieldStep {
   double cAx, cAy;
-  float cAxf, cAyf, pad0, pad1;
+  float cAxf, cAyf, cAxf_lo, cAyf_lo;
 };
 
 // One independent propagation problem.
@@ -121,11 +122,13 @@ struct Problem {
   void* ybuf0;              // y^ ping-pong
   void* ybuf1;
   const void* V;            // potential energy in S, or NULL
+  const void* Vlo;          // mixed path: V - (float)V as float, or NULL
   DevState* st;
   double* partials;         // 3 doubles per slot
   const ChebParams* cheb;
   double kx, ky, shift;     // c/(2dx) (order 2) or c/(12dx) (order 4); energy shift
-  float kxf, kyf;
+  float kxf, kyf;           // kx, ky rounded to FP32
+  float kxf_lo, kyf_lo;     // and their remainders
   PassCoef probe_coef;      // coefficients of the probe pass (stencil shift 0)
 };
 
@@ -142,6 +145,7 @@ struct LaunchParams {
   int conj_coef;            // 1: backward step (dt < 0): exp(+i H |dt|), the conjugate coefficients
   int async_tiles;          // FP32 basis: stage passes >= 3 by asynchronous copies (many tiles per CTA)
   int has_ay;               // 0: A_y = 0 in every step and problem (host: picks the kernel)
+  int diri;                 // Dirichlet boundaries (kernels that take the boundary at run time)
   double mcc, dt, tol;      // dt = |dt|
   const int* step;          // step counter of the running call (index into fields)
 };

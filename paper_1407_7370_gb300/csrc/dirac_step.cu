@@ -1,4 +1,4 @@
-// dirac_step.cu -- launcher of the one-launch time step (`lanczos_step`):
+// dirac_step.cu -- launcher of the FP64 one-launch time step (`lanczos_step`):
 // all Lanczos passes of a step of one problem and its recombination in one
 // cooperative launch, the passes separated by grid-wide barriers.  Kept in a
 // translation unit of its own so that it compiles in parallel with the
@@ -73,12 +73,10 @@ cudaError_t launch_step_s(int order, bool diri, bool hasv, const LaunchParams& p
 
 cudaError_t launch_step(int precision, int th, int order, bool diri, bool hasv, const LaunchParams& p, int n_sm,
                         const CoopArgs& ca, cudaStream_t s) {
-  if (precision == DIRAC_FP64) {
-    if (th == 16) return launch_step_s<double, 16>(order, diri, hasv, p, n_sm, ca, s);
-    return launch_step_s<double, 32>(order, diri, hasv, p, n_sm, ca, s);
-  }
-  if (th == 16) return launch_step_s<float, 16>(order, diri, hasv, p, n_sm, ca, s);
-  return launch_step_s<float, 32>(order, diri, hasv, p, n_sm, ca, s);
+  // the mixed path has its own one-launch step (dirac_step32.cu)
+  if (precision != DIRAC_FP64) return cudaErrorInvalidValue;
+  if (th == 16) return launch_step_s<double, 16>(order, diri, hasv, p, n_sm, ca, s);
+  return launch_step_s<double, 32>(order, diri, hasv, p, n_sm, ca, s);
 }
 
 }  // namespace dirac

@@ -235,7 +235,8 @@ def test_host_buffer_call_equals_device_call():
     ("fp64", "passes", 7 + 2 + 1),      # m passes + 2 spare launches for re-runs + recombine
     ("fp64", "one_launch", 1),
     ("fp64", "auto", 1),
-    ("mixed", "auto", 7 + 3 + 1),       # the mixed path keeps 2 + m / 5 spare launches
+    ("mixed", "passes", 7 + 3 + 1),     # the mixed path keeps 2 + m / 5 spare launches
+    ("mixed", "auto", 1),
     ("mixed", "one_launch", 1)])
 def test_kernel_launch_count(precision, mode, per_step):
     g = wl.Grid(32, 32, 0.1, 0.1)
@@ -437,6 +438,7 @@ def test_one_launch_step_agrees_with_per_pass_launches(precision, nx, ny, order,
     for s in range(6):
         op.A = tuple(A[s])
         ref, _ = lz.krylov_step(op, ref, 1e-4, 12, tol=tol)
+    # (the mixed input carries 5 % random noise, which fills the whole spectrum)
     tol_ref = fp64_tol(6, 1e-4) if precision == "fp64" else \
         mixed_tol(6, 1e-4, max(hnorm(g, tuple(a), V, order) for a in A))
     assert lz.rel_l2(b, ref) <= tol_ref
@@ -500,9 +502,17 @@ def test_laser_packet_1024_long_run_against_closed_form(precision):
 # ---------------------------------------------------------------------------
 # Mixed path: complex64 basis and FP32 stencil, FP64 scalars and state.
 # Tolerance: relative L2 of psi at most 1e-5 per unit of simulated time
-# against the FP64 oracle; for runs too short for that to exceed rounding,
-# FP32 rounding of one application of exp(-iH dt) per step, 2 u32 ||H|| dt
-# (u32 = 6e-8, ||H|| from the spectral bound of the discrete operator).
+# against the FP64 oracle.  Runs too short for that to exceed one step's
+# rounding get a floor:
+#  * packets propagated with the shift s = m c^2 (packet_tol): the part of a
+#    step that the mixed path holds in complex64 is the Krylov correction
+#    psi' - C_1 psi; its rounding, 4 u32 times its size per step, measured on
+#    the oracle's run (correction_sizes);
+#  * states without the shift, or random spinors that fill the whole
+#    spectrum (mixed_tol): their Krylov vectors carry every energy up to
+#    ||H||, and the FP32 rounding of one application of exp(-iH dt) per step,
+#    2 u32 ||H|| dt (u32 = 6e-8, ||H|| from the spectral bound of the
+#    discrete operator), is the floor.
 # ---------------------------------------------------------------------------
 def hnorm(grid, A=(0.0, 0.0), V=None, order=2, c=137.036):
     pf = 1.0 if order == 2 else 1.3723
@@ -514,6 +524,19 @@ def hnorm(grid, A=(0.0, 0.0), V=None, order=2, c=137.036):
 def mixed_tol(steps, dt, hn=None):
     floor = 0.0 if hn is None else 2 * 6e-8 * hn * dt * steps
     return max(1e-5 * steps * dt, floor)
+
+
+def correction_size(psi, psi_next):
+    """||psi' - <psi, psi'> psi / ||psi||^2|| / ||psi||: the part of one step
+    that is not a multiple of psi (the Krylov correction)."""
+    a = psi.reshape(-1)
+    b = psi_next.reshape(-1)
+    n2 = np.vdot(a, a).real
+    return float(np.linalg.norm(b - (np.vdot(a, b) / n2) * a) / np.sqrt(n2))
+
+
+def packet_tol(steps, dt, corrections):
+    return max(1e-5 * steps * dt, 4 * 6e-8 * float(np.sum(corrections)))
 
 
 def test_mixed_free_packet_64_full_run():
@@ -539,18 +562,36 @@ def test_mixed_ragged_and_boundary_grids(nx, ny, order, boundary, hasv, A):
     assert lz.rel_l2(out, ref) <= mixed_tol(steps, dt, hnorm(g, A, V, order))
 
 
-def test_mixed_step_scalars_match_oracle():
+@pytest.mark.parametrize("mode", ["one_launch", "passes"])
+def test_mixed_step_scalars_match_oracle(mode):
     g = wl.Grid(64, 48, 0.1, 0.1)
     psi0 = wl.positive_energy_packet(g, p0=(10.0, 5.0))
     V = wl.smoothed_coulomb(g, 3.0, 0.5)
-    dt, m = 1e-4, 12
-    out, info, _ = gpu_run(g, psi0, dt, m, 1, V=V, A=(4.0, -2.0), precision="mixed")
-    ref, oi = lz.krylov_step(oracle_op(g, V=V, A=(4.0, -2.0)), psi0.copy(), dt, m)
+    dt, m, s = 1e-4, 12, C * C
+    out, info, _ = gpu_run(g, psi0, dt, m, 1, V=V, A=(4.0, -2.0), precision="mixed", shift=s,
+                           step_mode=mode)
+    ref, oi = lz.krylov_step(oracle_op(g, V=V, A=(4.0, -2.0), shift=s), psi0.copy(), dt, m)
     assert info.k_used == oi.k_used == m
     assert abs(info.energy - oi.energy) <= 1e-9 * abs(oi.energy)
     assert abs(info.norm - oi.norm) <= 1e-7 * oi.norm
-    assert np.allclose(info.alpha[:4], oi.alpha[:4] / dt, rtol=1e-6)
-    assert lz.rel_l2(out, ref) <= mixed_tol(1, dt, hnorm(g, (4.0, -2.0), V))
+    # alpha of H - s: the oracle's are of dt (H - s)
+    assert np.allclose(info.alpha[:4], oi.alpha[:4] / dt, rtol=1e-6, atol=1e-6 * abs(oi.alpha[0] / dt))
+    assert lz.rel_l2(out, ref) <= packet_tol(1, dt, [correction_size(psi0, ref)])
+
+
+@pytest.mark.parametrize("p0", [(10.0, 0.0), (45.0, 10.0)])
+def test_mixed_packet_long_run_at_target(p0):
+    """A packet with the shift m c^2, 500 steps in a static field and a
+    potential, against the oracle at the mixed target 1e-5 per unit time
+    (no floor: the run is long enough for the target to exceed rounding)."""
+    g = wl.Grid(96, 80, 0.05, 0.05)
+    psi0 = wl.positive_energy_packet(g, p0=p0)
+    V = wl.smoothed_coulomb(g, 2.0, 0.5)
+    dt, m, steps, s = 2e-4, 16, 500, C * C
+    out, info, _ = gpu_run(g, psi0, dt, m, steps, V=V, A=(2.0, -1.0), precision="mixed", shift=s)
+    ref, _ = lz.propagate(oracle_op(g, V=V, A=(2.0, -1.0), shift=s), psi0.copy(), dt, m, steps)
+    err = lz.rel_l2(out, ref)
+    assert err <= 1e-5 * steps * dt, err
 
 
 @pytest.mark.slow
