@@ -19,10 +19,15 @@
 //   alpha_i  = sigma_i + P / X                         (Eq. 4)
 //   d_i      = P / X,   ||z_i - alpha_i q_i||^2 nu_i^2 = Y - P d_i =: s2_i
 //   beta_{i-1} = nu_i / (g_{i-1} nu_{i-1})               (a posteriori, exact)
-//   g_i = 1 / sqrt(s2_i),  e_{i+1} = sqrt(s2_i) / X,  sigma_{i+1} = alpha_i.
-// The shift sigma_i = alpha_{i-1} keeps s2 free of cancellation (Y ~ s2),
-// and beta_{i-1} is taken from the measured norm of the next vector rather
-// than from s2, so the tridiagonal T of Fig. 1 is reproduced to rounding.
+//   g_i = 1 / sqrt(s2_i),  e_{i+1} = sqrt(s2_i) / X.
+// The stencil shift sigma_i only moves rounding: any value gives the same T
+// in exact arithmetic.  It predicts alpha_i so that s2 is free of
+// cancellation (Y ~ s2): the previous step's alpha_i where there is one (T
+// changes little between steps), else alpha_{i-2} (the Krylov vectors of a
+// packet with a negative-energy admixture alternate between the two bands),
+// else alpha_{i-1}.  beta_{i-1} is taken from the measured norm of the next
+// vector rather than from s2, so the tridiagonal T of Fig. 1 is reproduced
+// to rounding.
 //
 // Work split: the tiles of all problems form one list of T tiles; persistent
 // CTA c of G takes a contiguous chunk of T / G or T / G + 1 tiles.  A CTA may hold SUB independent tile workers (groups
@@ -327,6 +332,12 @@ __device__ inline void finish_pass(const LaunchParams& lp, const Problem* pr, De
   const double alpha1_old = (i == 1) ? 0.0 : st->alpha[1];
   const double psi_norm_old = st->psi_norm, cum_old = st->cum_err;
   const int redo_left = st->redo_left;
+  // candidates for the next pass's stencil shift: alpha_{i+1} of the previous
+  // step (still in place: this step has not reached pass i + 1) and
+  // alpha_{i-1} of this one
+  const int k_prev = st->k_used;
+  const double alpha_next_prev = (i + 1 <= k_prev && i + 1 <= KMAX) ? st->alpha[i + 1] : 0.0;
+  const double alpha_im1 = (i >= 2) ? st->alpha[i - 1] : 0.0;
   const PassCoef pc_now = st->pc_cur;
   __syncwarp();   // every lane has read the state before lane 0 updates it
 
@@ -371,8 +382,17 @@ __device__ inline void finish_pass(const LaunchParams& lp, const Problem* pr, De
     if (i == 1) { st->psi_norm = nu; st->energy = alpha + shift; }
     if (s2 > 0.0) st->kappa_max = fmax(st->kappa_max, Y * rs * rs);
     if (!stop) {
-      st->sigma[i + 1] = alpha;
-      st->pc_cur = make_coef(rs, rs * dd, sq * rX, lp.mcc - shift - alpha, -lp.mcc - shift - alpha);
+      // The stencil shift of pass i + 1, a prediction of alpha_{i+1} (any
+      // value is exact; a close one keeps s2 free of cancellation).  T hardly
+      // changes from one step to the next -- for static fields its entries
+      // are moments of H in psi, which the propagation conserves -- so the
+      // previous step's alpha_{i+1} is the best guess when that step got so
+      // far.  Else alpha_{i-1}: the Krylov vectors of a positive-energy packet
+      // with a small negative-energy admixture alternate between the two
+      // bands, so alpha_{i+1} is close to alpha_{i-1}, not to alpha_i.
+      const double sig = (i + 1 <= k_prev) ? alpha_next_prev : (i >= 2 ? alpha_im1 : alpha);
+      st->sigma[i + 1] = sig;
+      st->pc_cur = make_coef(rs, rs * dd, sq * rX, lp.mcc - shift - sig, -lp.mcc - shift - sig);
       st->cur_pass = i + 1;
     }
   }
