@@ -211,11 +211,15 @@ cudaError_t launch_pass(int precision, int order, bool diri, bool hasv, const La
 }
 
 // Re-runs of a pass allowed per step (each costs one spare launch, which
-// exits at once when unused) and the cancellation ratio that triggers one:
-// with y^ stored to unit roundoff u, s2 = ||y^||^2 - P^2/X keeps about
-// u * kappa relative accuracy.
+// exits at once when unused) and the cancellation ratio kappa = Y / s2 that
+// triggers one.  With y^ stored to unit roundoff u, s2 = ||y^||^2 - P^2/X
+// keeps about u * kappa relative accuracy, and the rounding of P leaves a
+// component of about u sqrt(kappa) of q^_i in q^_{i+1}.  FP64: 1e12.  FP32:
+// 100, i.e. a pass whose stencil shift missed alpha_i by more than ten times
+// beta_i is re-run -- in practice pass 2 of a context's first step, before
+// the previous step's T can supply the shifts.
 int redo_budget(int precision, int m) { return precision == DIRAC_FP64 ? 2 : 2 + m / 5; }
-double kappa_redo(int precision) { return precision == DIRAC_FP64 ? 1e12 : 1e6; }
+double kappa_redo(int precision) { return precision == DIRAC_FP64 ? 1e12 : 1e2; }
 
 cudaError_t launch_recombine(int precision, const RecombParams& rp, int grid, cudaStream_t s) {
   if (precision == DIRAC_FP64) return launch_pdl(recombine<false>, grid, 256, 0, s, rp);

@@ -187,45 +187,52 @@ def test_autotune_leaves_states_and_picks_a_shape(tmp_path, monkeypatch):
     assert lz.rel_l2(psis[0].cpu().numpy(), ref) <= mixed_tol(2, 1e-4, hnorm(grid, np.zeros((1, 2)), V))
 
 
+def _oracle_pulse_run(g, psi0, dt, m, steps, a0, pulse, t0, shift):
+    """The oracle run of one batch problem (executed in a spawned process)."""
+    op = ham.Operator(g.nx, g.ny, g.dx, g.dy, shift=shift)
+    pk = wl.SinSquaredPulse(float(a0), pulse.omega, pulse.duration)
+    return lz.propagate(op, psi0.copy(), dt, m, steps, pk, t0)[0]
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
 def test_batch_256_full_size_sampled(precision):
     """The batched workload at its full size (256 packets on 128^2..512^2
     grids, m = 16, laser amplitudes up to 100 au), autotuned and replayed as
     a graph as the benchmark runs it: one problem of every grid size against
-    the oracle run alone (its own step means of the pulse)."""
-    from oracle import fields
+    the oracle run alone (its own step means of the pulse), over 20 steps
+    (the oracle runs in spawned processes while the GPU works)."""
+    import concurrent.futures
+    import multiprocessing
+
     from paper_1407_7370_gb300 import BatchPropagator
     from paper_1407_7370_gb300.propagator import pulse_sin2_mean
     cfg = wl.BATCH_256
     grids, p0s, a0s = wl.batch_packets(cfg["n"])
     m, dt, n, pulse = cfg["m"], cfg["dt"], cfg["n"], cfg["pulse"]
-    steps, C2 = 2, 137.036 ** 2
+    steps, C2 = 20, 137.036 ** 2
     t0 = 0.5   # mid-pulse, where A_x reaches a few au
-    base = np.array([pulse_sin2_mean(t0 + k * dt, dt, 1.0, pulse.omega, pulse.duration) for k in range(3)])
-    A = np.zeros((3, n, 2))
-    A[:, :, 0] = base[:, None] * a0s[None, :]
-    bp = BatchPropagator([(g.nx, g.ny, g.dx, g.dy) for g in grids], m_max=m, precision=precision)
-    for k in range(n):
-        bp.set_fields(k, shift=C2)
-    psi0 = [wl.positive_energy_packet(g, p0=(float(p), 0.0)) for g, p in zip(grids, p0s)]
-    psis = [torch.from_numpy(p.copy()).cuda() for p in psi0]
-    bp.autotune(psis, dt, m, A=A, steps=3)
-    bp.steps(psis, steps, dt, m, A=A[:steps])
     sample = [next(k for k, g in enumerate(grids) if g.nx == side) for side in (128, 256, 384, 512)]
-    for k in sample:
-        g = grids[k]
-        op = ham.Operator(g.nx, g.ny, g.dx, g.dy, shift=C2)
-        ref = psi0[k]
-        corr = []
-        for s in range(steps):
-            op.A = (a0s[k] * fields.step_mean(pulse, t0 + s * dt, dt), 0.0)
-            nxt, _ = lz.krylov_step(op, ref, dt, m)
-            corr.append(correction_size(ref, nxt))
-            ref = nxt
-        err = lz.rel_l2(psis[k].cpu().numpy(), ref)
-        tol = fp64_tol(steps, dt) if precision == "fp64" else packet_tol(steps, dt, corr)
-        assert err <= tol, (k, g.nx, err, tol)
+    psi0 = [wl.positive_energy_packet(g, p0=(float(p), 0.0)) for g, p in zip(grids, p0s)]
+    ctx = multiprocessing.get_context("spawn")
+    with concurrent.futures.ProcessPoolExecutor(max_workers=len(sample), mp_context=ctx) as pool:
+        futs = {k: pool.submit(_oracle_pulse_run, grids[k], psi0[k], dt, m, steps, a0s[k], pulse, t0, C2)
+                for k in sample}
+        base = np.array([pulse_sin2_mean(t0 + k * dt, dt, 1.0, pulse.omega, pulse.duration)
+                         for k in range(steps + 1)])
+        A = np.zeros((steps + 1, n, 2))
+        A[:, :, 0] = base[:, None] * a0s[None, :]
+        bp = BatchPropagator([(g.nx, g.ny, g.dx, g.dy) for g in grids], m_max=m, precision=precision)
+        for k in range(n):
+            bp.set_fields(k, shift=C2)
+        psis = [torch.from_numpy(p.copy()).cuda() for p in psi0]
+        bp.autotune(psis, dt, m, A=A[:3], steps=3)
+        bp.steps(psis, steps, dt, m, A=A[:steps])
+        for k in sample:
+            ref = futs[k].result()
+            err = lz.rel_l2(psis[k].cpu().numpy(), ref)
+            tol = fp64_tol(steps, dt) if precision == "fp64" else 1e-5 * steps * dt
+            assert err <= tol, (k, grids[k].nx, err, tol)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
