@@ -52,16 +52,17 @@ def STEP_BYTES_PER_SITE_MIXED(m):    # complex64 basis; psi read and written in 
 
 
 # DRAM traffic per launch from the last ncu capture of each kernel on the
-# configured grid, valid only for the kernel source it was taken with (sha1 of
-# dirac_kernels.cuh).
-TRAFFIC = {"lanczos_step<double>": ("fdb569ea81c3", 1.638726e9 + 1.302841e9),
-           "lanczos_pass<float>": ("fdb569ea81c3", 33.633280e6 + 0.583680e6)}
+# configured grid, valid only for the kernel sources it was taken with (sha1
+# of dirac_kernels.cuh and dirac_step32.cu).
+TRAFFIC = {}
 
 
 def kernel_sha() -> str:
     import hashlib
-    path = os.path.join(ROOT, "paper_1407_7370_gb300", "csrc", "dirac_kernels.cuh")
-    return hashlib.sha1(open(path, "rb").read()).hexdigest()[:12]
+    h = hashlib.sha1()
+    for name in ("dirac_kernels.cuh", "dirac_step32.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1407_7370_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:12]
 
 
 def traffic_for(kernel: str, grid):
@@ -71,6 +72,39 @@ def traffic_for(kernel: str, grid):
     if rec and rec[0] == kernel_sha():
         return rec[1]
     return None
+
+
+FP64_PEAK_DERIVED = 152 * 2 * 2 * 2.07e9 / 1e12   # TFLOP/s: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+
+
+def measured_alu_peaks():
+    """FP64 and FP32 FMA throughput measured on this GPU by the library's
+    dirac_measure_peak (TFLOP/s), or None."""
+    import ctypes
+    try:
+        from paper_1407_7370_gb300 import _native as nat
+        out = {}
+        for name, kind in (("fp64", nat.PEAK_FP64), ("fp32", nat.PEAK_FP32)):
+            t = ctypes.c_double(0.0)
+            nat.check(nat.lib().dirac_measure_peak(kind, ctypes.byref(t)))
+            out[name] = t.value
+        return out
+    except Exception:
+        return None
+
+
+def alu_roofline(achieved, alu, kernel, extra=None):
+    """Roofline of an FP64-bound kernel against the measured FP64 peak (the
+    derived one beside it)."""
+    peak = alu["fp64"] if alu else FP64_PEAK_DERIVED
+    r = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+         "kernel": kernel,
+         "peak_source": ("measured by dirac_measure_peak (FP64 FMA chains on every SM)" if alu
+                         else "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"),
+         "peak_derived": FP64_PEAK_DERIVED, "frac_of_derived": achieved / FP64_PEAK_DERIVED}
+    if extra:
+        r.update(extra)
+    return r
 
 
 def parse():
@@ -375,7 +409,7 @@ GS_FLOPS_PER_SITE_VECTOR = 64   # two Gram-Schmidt passes x (inner product 16 + 
 GS_BYTES_PER_SITE_VECTOR = 128  # two passes x (read q_j for the products + read q_j for the update)
 
 
-def measure_eigen(torch, gi, pk, side=None, iters=None):
+def measure_eigen(torch, gi, pk, side=None, iters=None, alu=None):
     """Eigenvalue mode on the 2048^2 smoothed-Coulomb workload: one untimed
     short call, then one timed call with per-kernel CUDA-event timing (side
     and iters override the grid and the iteration count, for profiling)."""
@@ -434,7 +468,6 @@ def measure_eigen(torch, gi, pk, side=None, iters=None):
     gs_ms = res.ms["dot"] + res.ms["update"]
     flops = GS_FLOPS_PER_SITE_VECTOR * n * k * (k + 1) / 2
     gbytes = GS_BYTES_PER_SITE_VECTOR * n * k * (k + 1) / 2
-    fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12
     achieved = flops / (gs_ms / 1e3) / 1e12
     hbm_peak = pk.get("hbm_gbs", 6800.0)
     out = {"workload": c["name"], "iterations": k, "seconds": t,
@@ -443,12 +476,9 @@ def measure_eigen(torch, gi, pk, side=None, iters=None):
            "n_found": int(res.values.size), "values_minus_mc2": [float(v) for v in res.values],
            "bounds": [float(b) for b in res.bounds], "breakdown": res.breakdown,
            "gpu_launches": res.launches, "kernel_ms": res.ms, "clocks": clk, "mixed": mixed,
-           "roofline": {"bound": "alu", "kernel": "eig_dot + eig_update (Gram-Schmidt, twice)",
-                        "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                        "frac": achieved / fp64_peak, "traffic": None,
-                        "share": gs_ms / max(1e-9, sum(res.ms.values())),
-                        "flops_per_site_vector": GS_FLOPS_PER_SITE_VECTOR,
-                        "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"},
+           "roofline": alu_roofline(achieved, alu, "eig_dot + eig_update (Gram-Schmidt, twice)",
+                                    {"traffic": None, "share": gs_ms / max(1e-9, sum(res.ms.values())),
+                                     "flops_per_site_vector": GS_FLOPS_PER_SITE_VECTOR}),
            "hbm": {"achieved": gbytes / (gs_ms / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
                    "frac": gbytes / (gs_ms / 1e3) / 1e9 / hbm_peak,
                    "bytes_per_site_vector": GS_BYTES_PER_SITE_VECTOR}}
@@ -510,7 +540,7 @@ def measure_paper_workload(torch, gi):
             "note": "the paper's time is one CPU process on a dual 8-core Xeon-E5 node: context"}
 
 
-def measure_adjoint(torch, gi, pk, steps=None):
+def measure_adjoint(torch, gi, pk, steps=None, alu=None):
     """The adjoint sweep of the 1024^2 gradient workload over `steps` steps (the
     full run is `full_steps` steps at the same cost per step), then a short
     profiled run for the contraction kernel's time."""
@@ -554,7 +584,6 @@ def measure_adjoint(torch, gi, pk, steps=None):
     n = g.n_sites
     per_launch = prof.info["ms_contract"] / 1e3 / c["ckpt"]
     flops = CONTRACT_FLOPS_PER_SITE * n / per_launch / 1e12
-    fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12
     out = {"workload": c["name"], "steps": c["steps"], "full_config_steps": c["full_steps"],
            "seconds": t, "ms_per_step": 1e3 * t / c["steps"],
            "value": n * c["steps"] / t, "unit": "site-steps/s of the gradient (forward + adjoint)",
@@ -562,13 +591,11 @@ def measure_adjoint(torch, gi, pk, steps=None):
            "ms_forward": res.info["ms_forward"], "ms_backward": res.info["ms_backward"],
            "quadrature_nodes": res.info["quadrature_nodes"], "gpu_launches": res.info["launches"],
            "loss": res.loss, "clocks": clk,
-           "roofline": {"bound": "alu", "kernel": "adj_contract<16> (per-site bilinear form)",
-                        "achieved": flops, "peak": fp64_peak, "unit": "TFLOP/s",
-                        "frac": flops / fp64_peak, "traffic": None,
-                        "kernel_avg_us": per_launch * 1e6,
-                        "flops_per_site": CONTRACT_FLOPS_PER_SITE,
-                        "share_of_backward": prof.info["ms_contract"] / max(1e-9, prof.info["ms_backward"]),
-                        "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"}}
+           "roofline": alu_roofline(flops, alu, "adj_contract<16> (per-site bilinear form)",
+                                    {"traffic": None, "kernel_avg_us": per_launch * 1e6,
+                                     "flops_per_site": CONTRACT_FLOPS_PER_SITE,
+                                     "share_of_backward": prof.info["ms_contract"] /
+                                     max(1e-9, prof.info["ms_backward"])})}
     prop.close()
     del Vs, psi0
     torch.cuda.empty_cache()
@@ -597,13 +624,14 @@ def run_ours(args):
     K, W = args.steps, args.warmup
     A = pulse_schedule(0.0, dt, W + 2 * K, pulse.a0, pulse.omega, pulse.duration)
     pk = peaks()
+    alu = measured_alu_peaks()
     hbm_peak = pk.get("hbm_gbs", 6800.0)
     hbm_src = "MEASURED_PEAKS.json hbm_gbs (burst copy)" if "hbm_gbs" in pk else "fallback 6.8 TB/s"
     if args.only in ("eigen", "adjoint", "batch", "paper"):   # one workload alone (profiling runs)
         if args.only == "eigen":
-            r = measure_eigen(torch, local, pk, args.eigen_side, args.eigen_iters)
+            r = measure_eigen(torch, local, pk, args.eigen_side, args.eigen_iters, alu)
         elif args.only == "adjoint":
-            r = measure_adjoint(torch, local, pk, args.adjoint_steps)
+            r = measure_adjoint(torch, local, pk, args.adjoint_steps, alu)
         elif args.only == "paper":
             r = measure_paper_workload(torch, local)
         else:
@@ -642,14 +670,20 @@ def run_ours(args):
     if args.only:
         r = runs[args.only]
         if rank == 0:
-            print(json.dumps({"partial": args.only, "ms_per_step": 1e3 * r["t"] / K,
-                              "value": site_rate(r["t"], K), "unit": UNIT}), flush=True)
+            ks = kernel_stats(r)
+            b = STEP_BYTES_PER_SITE_MIXED(m) if args.only == "mixed" else STEP_BYTES_PER_SITE(m)
+            if not ks["one_launch"]:
+                b = PASS_BYTES_PER_SITE_MIXED if args.only == "mixed" else PASS_BYTES_PER_SITE
+            gbs = b * g.n_sites / ks["launch_s"] / 1e9
+            print(json.dumps({"partial": args.only, "grid": g.nx, "ms_per_step": 1e3 * r["t"] / K,
+                              "value": site_rate(r["t"], K), "unit": UNIT, "kernel": ks,
+                              "alg_gbs": gbs, "hbm_frac": gbs / hbm_peak, "launches": r["launches"],
+                              "clocks": r["clocks"]}), flush=True)
         return 0
     bytes_step = g.n_sites * SITE_BYTES
     # FP64 path: bound by the FP64 pipe
     f = runs["fp64"]
     fk = kernel_stats(f)
-    fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12   # TFLOP/s: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz
     if fk["one_launch"]:
         f_kernel = "lanczos_step<double>"
         f_flops_site = (PASS_FLOPS_PER_SITE + RECOMB_FLOPS_PER_VECTOR) * m   # one launch = one step
@@ -658,12 +692,10 @@ def run_ours(args):
         f_kernel = "lanczos_pass<double>"
         f_flops_site, f_bytes_site = PASS_FLOPS_PER_SITE, PASS_BYTES_PER_SITE
     flops = f_flops_site * g.n_sites / fk["launch_s"] / 1e12
-    roofline = {"bound": "alu", "achieved": flops, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": flops / fp64_peak, "traffic": traffic_for(f_kernel, g),
-                "kernel": f_kernel, "kernel_avg_us": fk["launch_s"] * 1e6,
-                "kernel_share": fk["share"], "flops_per_site_per_launch": f_flops_site,
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz "
-                               "(probe measured 1.19 TFLOP/s)"}
+    roofline = alu_roofline(flops, alu, f_kernel,
+                            {"traffic": traffic_for(f_kernel, g), "kernel_avg_us": fk["launch_s"] * 1e6,
+                             "kernel_share": fk["share"], "flops_per_site_per_launch": f_flops_site,
+                             "fp32_peak_measured": alu["fp32"] if alu else None})
     f_gbs = f_bytes_site * g.n_sites / fk["launch_s"] / 1e9
     if roofline["traffic"] is not None:   # the ncu DRAM bytes of a launch over its live duration
         roofline["dram_gbs"] = roofline["traffic"] / fk["launch_s"] / 1e9
@@ -672,7 +704,7 @@ def run_ours(args):
     x = runs["mixed"]
     xk = kernel_stats(x)
     if xk["one_launch"]:
-        x_kernel, x_bytes_site = "lanczos_step<float>", STEP_BYTES_PER_SITE_MIXED(m)
+        x_kernel, x_bytes_site = "lanczos_step_m32", STEP_BYTES_PER_SITE_MIXED(m)
     else:
         x_kernel, x_bytes_site = "lanczos_pass<float>", PASS_BYTES_PER_SITE_MIXED
     x_gbs = x_bytes_site * g.n_sites / xk["launch_s"] / 1e9
@@ -731,9 +763,9 @@ def run_ours(args):
             line["batched"]["speedup_mixed_batched_vs_fp64_single"] = \
                 line["batched"]["mixed"]["value"] / line["value"]
         if not args.no_eigen:
-            line["eigen"] = measure_eigen(torch, local, pk, args.eigen_side, args.eigen_iters)
+            line["eigen"] = measure_eigen(torch, local, pk, args.eigen_side, args.eigen_iters, alu)
         if not args.no_adjoint:
-            line["adjoint"] = measure_adjoint(torch, local, pk, args.adjoint_steps)
+            line["adjoint"] = measure_adjoint(torch, local, pk, args.adjoint_steps, alu)
         if not args.no_paper_workload:
             line["paper_workload"] = measure_paper_workload(torch, local)
         if not args.no_cpu_baseline and world == 1:
