@@ -372,19 +372,29 @@ def measure_batch(args, torch, world, dist, gi, pk):
         sub.close()
         pass_ms, pass_n = prof["pass"]
         rec_ms, rec_n = prof["recombine"]
-        sb = 16 if prec == "mixed" else 32
-        # launch-average pass time covers the spare launches too: use the
-        # pass time per step divided by m (the algorithmic passes)
-        per_pass = pass_ms / 1e3 / steps / m
-        gbs = 3 * sb * sites / per_pass / 1e9
+        step_ms, step_n = prof.get("step", (0.0, 0))
+        hbm = pk.get("hbm_gbs", 6800.0)
+        if step_n:   # one launch per step (all passes of every problem and the recombination)
+            b = STEP_BYTES_PER_SITE_MIXED(m) if prec == "mixed" else STEP_BYTES_PER_SITE(m)
+            gbs = b * sites / (step_ms / 1e3 / step_n) / 1e9
+            hbm_alg = {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                       "kernel": "lanczos_step_m32" if prec == "mixed" else "lanczos_step<double>",
+                       "kernel_avg_us": 1e3 * step_ms / step_n, "bytes_per_site_per_step": b}
+        else:
+            sb = 16 if prec == "mixed" else 32
+            # launch-average pass time covers the spare launches too: use the
+            # pass time per step divided by m (the algorithmic passes)
+            per_pass = pass_ms / 1e3 / steps / m
+            gbs = 3 * sb * sites / per_pass / 1e9
+            hbm_alg = {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                       "kernel": "lanczos_pass", "bytes_per_site_per_pass": 3 * sb}
         out[prec] = {"value": world * sites * m * steps / t, "unit": UNIT,
                      "ms_per_step": 1e3 * t / steps, "steps": steps, "gpu_launches": launches,
                      "autotune": tune, "clocks": clk,
                      "pass_time_per_step_ms": pass_ms / steps, "recombine_ms_per_step": rec_ms / steps,
+                     "step_kernel_ms_per_step": step_ms / steps,
                      "kappa_max": max(i.kappa_max for i in infos),
-                     "hbm_algorithmic": {"achieved": gbs, "peak": pk.get("hbm_gbs", 6800.0),
-                                         "unit": "GB/s", "frac": gbs / pk.get("hbm_gbs", 6800.0),
-                                         "bytes_per_site_per_pass": 3 * sb}}
+                     "hbm_algorithmic": hbm_alg}
         bp.close()
         del psis
         torch.cuda.empty_cache()
