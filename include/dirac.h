@@ -284,15 +284,26 @@ dirac_status dirac_use_graphs(dirac_ctx* ctx, int enable);
  *     barrier every CTA sums all CTA partials in the same order and updates
  *     its own copy of the scalars.  Each barrier wait is bounded: a timeout
  *     ends the launch and the next read of the state reports DIRAC_ECUDA.
+ *     On the mixed path the tiles are staged by tensor copies into a
+ *     shared-memory ring by a producer warp, and batches run every problem
+ *     in the same launch.
  *   DIRAC_STEP_AUTO (default): one launch per step on the FP64 path (one
- *     CTA per SM), per-pass launches on the mixed path (eight CTAs per SM,
- *     where the barrier costs more than the launch boundaries).
+ *     CTA per SM), per-pass launches on the mixed path (eight CTAs per SM;
+ *     measured faster there than the one-launch form).
  * Results agree to rounding: the partial sums are added in another order.
  */
 #define DIRAC_STEP_AUTO 0
 #define DIRAC_STEP_PASSES 1
 #define DIRAC_STEP_ONE_LAUNCH 2
 dirac_status dirac_set_step_mode(dirac_ctx* ctx, int mode);
+
+/*
+ * The same choice for a batch (mixed precision: DIRAC_STEP_ONE_LAUNCH runs
+ * every pass of every problem and the recombination as one cooperative
+ * launch per step; FP64 batches always use per-pass launches).
+ * Errors: DIRAC_EINVAL (null batch, unknown mode).
+ */
+dirac_status dirac_batch_set_step_mode(dirac_batch* batch, int mode);
 
 /*
  * Test of the failure path of the one-launch step: runs one step whose grid

@@ -132,6 +132,7 @@ def lib():
         "dirac_batch_use_graphs": (i, [vp, i]),
         "dirac_use_graphs": (i, [vp, i]),
         "dirac_set_step_mode": (i, [vp, i]),
+        "dirac_batch_set_step_mode": (i, [vp, i]),
         "dirac_debug_barrier_timeout": (i, [vp, vp, d, i]),
         "dirac_profile_read": (i, [vp, dp, ctypes.POINTER(ctypes.c_longlong)]),
         "dirac_apply_hamiltonian": (i, [vp, vp, vp]),

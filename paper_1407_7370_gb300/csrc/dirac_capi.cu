@@ -5,6 +5,7 @@
 #include "dirac_kernels.cuh"
 
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <atomic>
@@ -115,6 +116,47 @@ dirac_status make_cheb(double c0, double half, double dt, double shift, ChebPara
     }
   }
   return DIRAC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// tensor maps of the mixed one-launch step
+// ---------------------------------------------------------------------------
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (the
+// library does not link against the driver library itself)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static std::atomic<void*> fn{nullptr};
+  void* f = fn.load();
+  if (!f) {
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !f)
+      return nullptr;
+    fn.store(f);
+  }
+  return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+}
+
+// Map of `fields` consecutive nx x ny spinor fields (byte stride fstride
+// between fields) as a tensor of FP32 (complex64 spinors, 4 floats per site)
+// or FP64 (complex128) elements, of rank 3 ({4 nx, ny, fields}) or, with
+// fields = 0, rank 2, with a box of one tile and its halo, 4 (32 + 2R) x
+// (th + 2R) (x 1) elements, zeros outside.  False if the driver refuses the
+// shape (the kernel then copies row by row).
+bool encode_field_map(CUtensorMap* map, bool fp64, const void* base, int nx, int ny, int fields, size_t fstride,
+                      int R, int th) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t eb = fp64 ? 8 : 4;
+  const cuuint64_t dims[3] = {4ull * (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)(fields > 0 ? fields : 1)};
+  const cuuint64_t strides[2] = {4ull * (cuuint64_t)nx * eb, (cuuint64_t)fstride};
+  const cuuint32_t box[3] = {(cuuint32_t)(4 * (TILE_W + 2 * R)), (cuuint32_t)(th + 2 * R), 1u};
+  const cuuint32_t es[3] = {1u, 1u, 1u};
+  const CUresult r = enc(map, fp64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                         fields > 0 ? 3u : 2u, const_cast<void*>(base), dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
 }
 
 // ---------------------------------------------------------------------------
@@ -281,6 +323,13 @@ struct HostProblem {
   double vmin = 0, vmax = 0;
   double ax = 0, ay = 0, shift = 0;
   bool fields_set = false;
+  // mixed precision: tensor maps of the complex64 fields (set at creation)
+  // and of the state (re-encoded when the state's address changes)
+  CUtensorMap map_basis{}, map_ybuf{};
+  bool map_v_ok = false;
+  CUtensorMap map_psi{};
+  const void* map_psi_addr = nullptr;
+  bool map_psi_ok = false;
 };
 
 struct Engine {
@@ -330,8 +379,10 @@ struct Engine {
     return step_mode == DIRAC_STEP_AUTO || step_mode == DIRAC_STEP_ONE_LAUNCH;
   }
   // mixed precision, any number of problems: one cooperative launch per step
-  // (lanczos_step_m32) unless per-pass launches are asked for
-  bool use_m32() const { return precision == DIRAC_MIXED && step_mode != DIRAC_STEP_PASSES; }
+  // (lanczos_step_m32) when asked for; per-pass launches are the default
+  // (measured faster: 1024^2 0.60 vs 0.65 ms per step, the 256-packet batch
+  // 10.8 vs 12.3 ms)
+  bool use_m32() const { return precision == DIRAC_MIXED && step_mode == DIRAC_STEP_ONE_LAUNCH; }
   cudaError_t mark(int kind);
   dirac_status init(int n, const int* nx, const int* ny, const double* dx, const double* dy, double mass_,
                     double c_, int order_, int boundary_, int precision_, int m_max_, void* stream_);
@@ -430,6 +481,11 @@ dirac_status Engine::init(int n, const int* nx, const int* ny, const double* dx,
     q.basis = p; p += (size_t)nbasis * f;
     q.ybuf[0] = p; p += f;
     q.ybuf[1] = p; p += f;
+    if (precision == DIRAC_MIXED) {   // the basis vectors are packed; the y^ buffers `f` apart
+      q.map_v_ok = encode_field_map(&q.map_basis, false, q.basis, q.nx, q.ny, nbasis, (size_t)q.n * sb,
+                                    order / 2, M32_TILE_H) &&
+                   encode_field_map(&q.map_ybuf, false, q.ybuf[0], q.nx, q.ny, 2, f, order / 2, M32_TILE_H);
+    }
   }
   CUDA_TRY(cudaMalloc(&d_partials, 3 * sizeof(double) * std::max<size_t>(slots, 1)));
   CUDA_TRY(cudaMalloc(&d_st, sizeof(DevState) * n));
@@ -570,7 +626,8 @@ dirac_status Engine::run(vec4* const* psi, int nsteps, double dt, int m, double 
   const int nfield = a_xy ? nsteps * np : np;
   const size_t off_cheb = align256(sizeof(Problem) * np);
   const size_t off_field = off_cheb + align256(sizeof(ChebParams) * np);
-  const size_t bytes = off_field + align256(sizeof(FieldStep) * nfield);
+  const size_t off_maps = off_field + align256(sizeof(FieldStep) * nfield);
+  const size_t bytes = off_maps + (m32 ? align256(sizeof(TmaMaps) * np) : 0);
   if (tab_ev_live) CUDA_TRY(cudaEventSynchronize(tab_ev));   // staging free again
   if (bytes > tab_cap) {
     CUDA_TRY(cudaStreamSynchronize(stream));
@@ -587,6 +644,7 @@ dirac_status Engine::run(vec4* const* psi, int nsteps, double dt, int m, double 
   Problem* hp = reinterpret_cast<Problem*>(hb);
   ChebParams* hc = reinterpret_cast<ChebParams*>(hb + off_cheb);
   FieldStep* hf = reinterpret_cast<FieldStep*>(hb + off_field);
+  TmaMaps* hm = m32 ? reinterpret_cast<TmaMaps*>(hb + off_maps) : nullptr;
   const double kfac = (order == 2) ? 2.0 : 12.0;
   const double mcc = mass * c * c;
   bool hasv = false;
@@ -626,6 +684,16 @@ dirac_status Engine::run(vec4* const* psi, int nsteps, double dt, int m, double 
     d.kyf_lo = (float)(d.ky - (double)d.kyf);
     d.shift = q.shift;
     d.probe_coef = make_coef(1.0, 0.0, 0.0, mcc - q.shift, -mcc - q.shift);
+    if (m32) {
+      if (q.map_psi_addr != psi[b]) {
+        q.map_psi_ok = encode_field_map(&q.map_psi, true, psi[b], q.nx, q.ny, 0, 0, order / 2, M32_TILE_H);
+        q.map_psi_addr = psi[b];
+      }
+      hm[b].basis = q.map_basis;
+      hm[b].ybuf = q.map_ybuf;
+      hm[b].psi = q.map_psi;
+      d.tma = (q.map_v_ok && q.map_psi_ok) ? 1 : 0;
+    }
     hasv = hasv || q.has_v;
   }
   bool has_ay = false;
@@ -650,6 +718,7 @@ dirac_status Engine::run(vec4* const* psi, int nsteps, double dt, int m, double 
   LaunchParams lp;
   std::memset(&lp, 0, sizeof(lp));
   lp.probs = reinterpret_cast<const Problem*>(d_tab);
+  lp.maps = m32 ? reinterpret_cast<const TmaMaps*>(db + off_maps) : nullptr;
   lp.states = d_st;
   lp.fields = reinterpret_cast<const FieldStep*>(db + off_field);
   lp.fstride = a_xy ? np : 0;
@@ -1222,6 +1291,14 @@ dirac_status dirac_set_step_mode(dirac_ctx* ctx, int mode) {
   if (mode != DIRAC_STEP_AUTO && mode != DIRAC_STEP_PASSES && mode != DIRAC_STEP_ONE_LAUNCH)
     return fail(DIRAC_EINVAL, "unknown step mode %d", mode);
   ctx->e.step_mode = mode;
+  return DIRAC_OK;
+}
+
+dirac_status dirac_batch_set_step_mode(dirac_batch* bt, int mode) {
+  if (!bt) return fail(DIRAC_EINVAL, "null batch");
+  if (mode != DIRAC_STEP_AUTO && mode != DIRAC_STEP_PASSES && mode != DIRAC_STEP_ONE_LAUNCH)
+    return fail(DIRAC_EINVAL, "unknown step mode %d", mode);
+  bt->e.step_mode = mode;
   return DIRAC_OK;
 }
 

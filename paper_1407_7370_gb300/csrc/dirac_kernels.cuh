@@ -50,6 +50,7 @@
 // complex64 basis and y^, FP32 stencil, warp sums converted to FP64, FP64
 // scalars; q^_1 is the complex128 state itself (passes 1-2 read it).
 #pragma once
+#include <cuda.h>           // CUtensorMap (the type only; the library calls the driver through the runtime)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -134,11 +135,25 @@ struct Problem {
   double kx, ky, shift;     // c/(2dx) (order 2) or c/(12dx) (order 4); energy shift
   float kxf, kyf;           // kx, ky rounded to FP32
   float kxf_lo, kyf_lo;     // and their remainders
+  int tma;                  // the mixed one-launch step stages tiles by tensor copies (maps valid)
   PassCoef probe_coef;      // coefficients of the probe pass (stencil shift 0)
+};
+
+// Tensor maps of one problem for the bulk tensor copies of the mixed
+// one-launch step, each with a box of one tile and its halo and zeros
+// outside the grid: `basis` covers the complex64 basis vectors q^_2 ..
+// (packed, nx ny 16 bytes apart) as a 3D FP32 tensor {4 nx, ny, vectors},
+// `ybuf` the two y^ buffers as {4 nx, ny, 2}, `psi` the complex128 state as a
+// 2D FP64 tensor {4 nx, ny}.
+struct TmaMaps {
+  CUtensorMap basis;
+  CUtensorMap ybuf;
+  CUtensorMap psi;
 };
 
 struct LaunchParams {
   const Problem* probs;
+  const TmaMaps* maps;      // one per problem (mixed one-launch step only), else NULL
   int redo_budget;          // re-runs allowed per step (the spare launches)
   double kappa_redo;        // re-run a pass whose ||y^||^2 / s2 exceeds this
   DevState* states;         // one per problem, same order
@@ -172,6 +187,24 @@ __device__ __forceinline__ S warp_sum(S v) {
   return v;
 }
 
+// ---------------------------------------------------------------------------
+// compensated FP32 arithmetic (value s plus error accumulator e)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& r) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  r = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// s + e  +=  (kh + kl) * a
+__device__ __forceinline__ void acc_prod(float kh, float kl, float a, float& s, float& e) {
+  const float p = __fmul_rn(kh, a);
+  const float pe = fmaf(kh, a, -p);
+  float t, r;
+  two_sum(s, p, t, r);
+  s = t;
+  e = __fadd_rn(e, __fadd_rn(pe, r));
+  e = fmaf(kl, a, e);
+}
 // grid coordinate -> array index; `outside` marks a Dirichlet zero
 template <bool DIRI>
 __device__ __forceinline__ int wrap(int g, int n, bool& outside) {
@@ -572,6 +605,9 @@ __device__ __forceinline__ void pass_body(const LaunchParams& lp, const DevState
     const S cAx = F32 ? (S)fs.cAxf : (S)fs.cAx, cAy = F32 ? (S)fs.cAyf : (S)fs.cAy;
     const S au_hi = F32 ? (S)pc.au_hi : (S)pc.au0, au_lo = F32 ? (S)pc.au_lo : S(0);
     const S ad_hi = F32 ? (S)pc.ad_hi : (S)pc.ad0, ad_lo = F32 ? (S)pc.ad_lo : S(0);
+    // FP32: remainders of the stencil and vector-potential coefficients
+    const S kx_lo = F32 ? (S)pr->kxf_lo : S(0), ky_lo = F32 ? (S)pr->kyf_lo : S(0);
+    const S cAx_lo = F32 ? (S)fs.cAxf_lo : S(0), cAy_lo = F32 ? (S)fs.cAyf_lo : S(0);
     const int nx = pr->nx, ny = pr->ny;
     const size_t n = (size_t)nx * ny;
     // this pass's vectors
@@ -585,6 +621,7 @@ __device__ __forceinline__ void pass_body(const LaunchParams& lp, const DevState
     const T4* yprev = static_cast<const T4*>(y_prev);
     const bool q64 = !F32 || i <= 2;                // q^_{i-1} stored as complex128
     const S* Vp = static_cast<const S*>(pr->V);   // NULL: V = 0 for this problem
+    const float* Vlo = static_cast<const float*>(pr->Vlo);   // mixed path: V - (float)V, or NULL
 
     // q^_i at grid point (gx, gy) (zero outside for Dirichlet) into smem slot
     auto form = [&](int gx, int gy, int row, int col, S (&qp)[4]) {
@@ -619,11 +656,22 @@ __device__ __forceinline__ void pass_body(const LaunchParams& lp, const DevState
     // (qp) and V; stores q^_i and y^_i and accumulates P, Y, X
     auto site_update = [&](size_t idx, const S (&C)[4], const S (&dxv)[4], const S (&dyv)[4],
                            const S (&qp)[4]) {
-      S au, ad;
+      S au, ad, aul = au_lo, adl = ad_lo;
       if (HAS_V && Vp != nullptr) {   // V stored in S (float copy on the mixed path)
         const S v = Vp[idx];
-        au = au_hi + v;
-        ad = ad_hi + v;
+        if constexpr (F32) {
+          // the FP32 sum with the diagonal (up to 2 m c^2) rounds differently at
+          // every site: its error and V's own remainder go into the low part
+          float ru, rd;
+          two_sum(au_hi, v, au, ru);
+          two_sum(ad_hi, v, ad, rd);
+          const float vl = Vlo ? Vlo[idx] : 0.f;
+          aul = au_lo + vl + ru;
+          adl = ad_lo + vl + rd;
+        } else {
+          au = au_hi + v;
+          ad = ad_hi + v;
+        }
       } else {
         au = au_hi;
         ad = ad_hi;
@@ -643,10 +691,16 @@ __device__ __forceinline__ void pass_body(const LaunchParams& lp, const DevState
         yv[3] = fma(cAy, C[0], yv[3]);
       }
       if constexpr (F32) {
-        yv[0] = fma(au_lo, C[0], yv[0]);
-        yv[1] = fma(au_lo, C[1], yv[1]);
-        yv[2] = fma(ad_lo, C[2], yv[2]);
-        yv[3] = fma(ad_lo, C[3], yv[3]);
+        yv[0] = fma(aul, C[0], fma(kx_lo, dxv[3], fma(-ky_lo, dyv[2], fma(cAx_lo, C[2], yv[0]))));
+        yv[1] = fma(aul, C[1], fma(-kx_lo, dxv[2], fma(-ky_lo, dyv[3], fma(cAx_lo, C[3], yv[1]))));
+        yv[2] = fma(adl, C[2], fma(kx_lo, dxv[1], fma(ky_lo, dyv[0], fma(cAx_lo, C[0], yv[2]))));
+        yv[3] = fma(adl, C[3], fma(-kx_lo, dxv[0], fma(ky_lo, dyv[1], fma(cAx_lo, C[1], yv[3]))));
+        if constexpr (HAS_AY) {
+          yv[0] = fma(cAy_lo, C[3], yv[0]);
+          yv[1] = fma(-cAy_lo, C[2], yv[1]);
+          yv[2] = fma(-cAy_lo, C[1], yv[2]);
+          yv[3] = fma(cAy_lo, C[0], yv[3]);
+        }
       }
       if (i >= 2) {
 #pragma unroll
@@ -857,11 +911,53 @@ lanczos_pass(const __grid_constant__ LaunchParams lp) {
   asm volatile("griddepcontrol.launch_dependents;");
 }
 
+// psi <- C_1 psi + sum_{j >= 2} C_j q^_j at site s: the complex64 basis
+// terms accumulated in compensated FP32 (coefficients as FP32 pairs, exact
+// products, two-sum accumulation), added to the FP64 term C_1 psi at the end.
+// Loads of sixteen basis vectors are issued before their products.
+__device__ __forceinline__ void recombine_site_df(vec4* psi, const float4* basis, size_t n, size_t s, int k,
+                                                  const double* cr, const double* ci, const float* crh,
+                                                  const float* crl, const float* cih, const float* cil) {
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, e0 = 0.f, e1 = 0.f, e2 = 0.f, e3 = 0.f;
+  for (int j0 = 2; j0 <= k; j0 += 16) {
+    float4 v[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+      if (j0 + u <= k) v[u] = __ldcs(basis + (size_t)(j0 + u - 2) * n + s);
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      if (j0 + u <= k) {
+        const int j = j0 + u;
+        const float ah = crh[j], al = crl[j], bh = cih[j], bl = cil[j];
+        // (a + i b)(q.re + i q.im) for the upper (x, y) and lower (z, w) component
+        acc_prod(ah, al, v[u].x, s0, e0);
+        acc_prod(-bh, -bl, v[u].y, s0, e0);
+        acc_prod(ah, al, v[u].y, s1, e1);
+        acc_prod(bh, bl, v[u].x, s1, e1);
+        acc_prod(ah, al, v[u].z, s2, e2);
+        acc_prod(-bh, -bl, v[u].w, s2, e2);
+        acc_prod(ah, al, v[u].w, s3, e3);
+        acc_prod(bh, bl, v[u].z, s3, e3);
+      }
+    }
+  }
+  const vec4 q = psi[s];
+  const double ar = cr[1], ai = ci[1];
+  vec4 o;
+  o.x = fma(ar, q.x, fma(-ai, q.y, (double)s0 + (double)e0));
+  o.y = fma(ar, q.y, fma(ai, q.x, (double)s1 + (double)e1));
+  o.z = fma(ar, q.z, fma(-ai, q.w, (double)s2 + (double)e2));
+  o.w = fma(ar, q.w, fma(ai, q.z, (double)s3 + (double)e3));
+  psi[s] = o;
+}
+
 // ---------------------------------------------------------------------------
 // psi <- sum_j C_j q^_j (Eq. 17), q^_1 = psi, q^_j = basis[j-2] for j >= 2.
 // FP64 path: complex128 throughout.  Mixed path: the basis is complex64;
 // C_1 psi is formed in FP64 so that the FP32 rounding of the basis only
-// enters the (small) Krylov corrections.
+// enters the (small) Krylov corrections, and those are summed with
+// compensation (recombine_site_df): plain FP32 accumulation of the
+// corrections was the largest error of the mixed path on fast packets.
 // Blocks are dealt to problems in proportion to their size.
 // ---------------------------------------------------------------------------
 template <bool MIXED>
@@ -912,17 +1008,20 @@ template <bool MIXED>
 __global__ void __launch_bounds__(256) recombine(const __grid_constant__ RecombParams rp) {
   asm volatile("griddepcontrol.wait;" ::: "memory");
   __shared__ double cr[KMAX + 2], ci[KMAX + 2];
-  __shared__ float fr[KMAX + 2], fi[KMAX + 2];
+  __shared__ float fr[KMAX + 2], fi[KMAX + 2], frl[KMAX + 2], fil[KMAX + 2];
   __shared__ int k_s, err_s;
   const int b = rp.blk_prob[blockIdx.x];
   const Problem* pr = rp.probs + b;
   DevState* st = pr->st;
   if (threadIdx.x == 0) { k_s = st->k_used; err_s = st->error; }
   if (threadIdx.x <= KMAX) {
-    cr[threadIdx.x] = st->coef_re[threadIdx.x];
-    ci[threadIdx.x] = st->coef_im[threadIdx.x];
-    fr[threadIdx.x] = (float)cr[threadIdx.x];
-    fi[threadIdx.x] = (float)ci[threadIdx.x];
+    const double a = st->coef_re[threadIdx.x], c = st->coef_im[threadIdx.x];
+    cr[threadIdx.x] = a;
+    ci[threadIdx.x] = c;
+    fr[threadIdx.x] = (float)a;
+    fi[threadIdx.x] = (float)c;
+    frl[threadIdx.x] = (float)(a - (double)fr[threadIdx.x]);
+    fil[threadIdx.x] = (float)(c - (double)fi[threadIdx.x]);
   }
   __syncthreads();
   const int lb = blockIdx.x - pr->rblk_begin;
@@ -937,8 +1036,13 @@ __global__ void __launch_bounds__(256) recombine(const __grid_constant__ RecombP
   const long long n = (long long)pr->nx * pr->ny;
   const long long stride = (long long)pr->rblk_count * blockDim.x;
   vec4* psi = const_cast<vec4*>(pr->psi);
-  for (long long s = (long long)lb * blockDim.x + threadIdx.x; s < n; s += stride)
-    recombine_site<MIXED>(psi, pr->basis, n, s, k, cr, ci, fr, fi);
+  for (long long s = (long long)lb * blockDim.x + threadIdx.x; s < n; s += stride) {
+    if constexpr (MIXED)
+      recombine_site_df(psi, static_cast<const float4*>(pr->basis), (size_t)n, (size_t)s, k, cr, ci, fr, frl, fi,
+                        fil);
+    else
+      recombine_site<false>(psi, pr->basis, n, s, k, cr, ci, fr, fi);
+  }
   asm volatile("griddepcontrol.launch_dependents;");
 }
 

@@ -1,47 +1,38 @@
 // dirac_step32.cu -- the mixed-precision time step as one cooperative launch:
 // every Lanczos pass (Fig. 1, Eq. 4) of every problem of a table and the
 // recombination (Eq. 17), with the tiles of each pass streamed into shared
-// memory by bulk asynchronous copies, and the stencil product and the
-// recombination evaluated in compensated FP32 arithmetic.
+// memory by bulk asynchronous tensor copies, and the recombination summed in
+// compensated FP32 arithmetic.
 //
-// Launch: one CTA per SM, all resident (cooperative), each owning the same
+// Launch: every CTA resident (cooperative; two per SM where the shared
+// memory allows, for more warps to hide latency), each owning the same
 // contiguous chunk of the tile list in every pass (the tiles it writes in a
 // pass are the ones it reads in the next, apart from halos).  Warp roles:
-//   * producer (the last warp): for each tile of the chunk, the rows of the
-//     tile and its halo of the pass's two input fields (y^_{i-1} and
-//     q^_{i-1}; the complex128 state psi in passes 1 and 2) are copied into a
-//     ring of STAGES shared-memory stages with cp.async.bulk, one copy per row
-//     piece (a row that wraps around a periodic boundary is two or three
-//     pieces), completion counted in bytes on the stage's "full" mbarrier.
-//     Dirichlet zeros and grids narrower than a tile row are written by the
-//     producer's threads themselves before they arrive on the barrier.
+//   * producer (the last warp): for each tile of the chunk, the tile and its
+//     halo of the pass's two input fields (y^_{i-1} and q^_{i-1}; the
+//     complex128 state psi in passes 1 and 2) are copied into a ring of
+//     STAGES shared-memory stages by one tensor copy per field (a box of
+//     (32 + 2R) x (16 + 2R) sites; zeros outside the grid), completion counted
+//     in bytes on the stage's "full" mbarrier.  Where the driver refuses a
+//     tensor map the rows are copied one by one with cp.async.bulk instead.
 //   * consumers (NCW warps): wait for a stage, form q^_i = g y^_{i-1} -
 //     gd q^_{i-1} on the tile and its halo into a formed-tile buffer, release
 //     the stage, then apply the stencil, store q^_i and y^_i, and accumulate
 //     P = Re<q^_i, y^_i>, Y = ||y^_i||^2, X = ||q^_i||^2 (FP32 within a tile,
-//     FP64 across tiles and threads).
+//     compensated FP32 across a thread's tiles, FP64 across threads).
 // Between passes: a bounded grid barrier.  One problem: every CTA sums all CTA
 // partials in the same order and updates its own shared-memory copy of the
 // scalars (identical everywhere).  Several problems: the last CTA to finish a
 // problem's tiles sums that problem's partials and updates its scalars in
 // global memory before the barrier (as the per-pass kernel does).
 //
-// Compensated stencil.  With energies relative to m c^2, the lower
-// component of (H - s - sigma) q is a near cancellation between the diagonal
-// term (about -2 m c^2 d) and the kinetic terms c (-i D_x + D_y) u, and the
-// upper one between -sigma u and c (-i D_x - D_y) d.  Plain FP32 arithmetic
-// rounds each of these large terms, and that rounding -- not the FP32 storage
-// of the vectors -- dominated the mixed path's error on fast packets.  Here
-// every difference q[j+1] - q[j-1] is split exactly into a rounded value and
-// its error (two-sum), every product of a stored value with a coefficient
-// exactly into a product and its error (fused multiply-add), and the terms of
-// each output are summed with compensation (two-sum), the error terms
-// gathered in a second FP32 accumulator; coefficients (c / 2dx, c A, the
-// diagonal m c^2 - s - sigma + V) enter as FP32 pairs (value plus remainder).
-// The result is (H - s - sigma) q for the stored q to about u_32^2 relative
-// to the largest term, then rounded once to FP32.  The recombination sums
-// its complex64 terms the same way: with FP32 accumulation its rounding was
-// the next largest error on fast packets.
+// Precision.  The stencil product runs in FP32 on the complex64 tile, each
+// coefficient (c / 2dx, c A, the diagonal m c^2 - s - sigma + V) entering as
+// an FP32 value plus its remainder.  The recombination sums its complex64
+// terms with compensation (exact products, two-sum accumulation): measured
+// on 500 steps of the fastest packets of the batched workload, plain FP32
+// accumulation there tripled the error, while a compensated stencil product
+// did not lower the largest error.
 #include "dirac.h"
 #include "dirac_internal.h"
 #include "dirac_kernels.cuh"
@@ -60,19 +51,21 @@ constexpr int NCW = 8;             // consumer warps
 constexpr int NC = 32 * NCW;       // consumer threads
 constexpr int NT = NC + 32;        // and the producer warp
 constexpr int RPT = TH / NCW;      // rows per consumer thread
-constexpr int STAGES = 5;          // shared-memory ring depth
+constexpr int STAGES = 3;          // shared-memory ring depth (two CTAs share an SM)
 constexpr long long WAIT_CYCLES = 4000000000LL;   // bounded waits: about two seconds at 2 GHz
+
+constexpr int round128(int b) { return (b + 127) & ~127; }
 
 template <int R>
 struct Geo {
   static constexpr int W = TILE_W + 2 * R;   // row of a tile with its halo
   static constexpr int HR = TH + 2 * R;      // rows with the halo
   static constexpr int NS = W * HR;          // sites of the rectangle
-  static constexpr int A_BYTES = NS * 16;    // y^_{i-1}: complex64 spinors
-  static constexpr int B_BYTES = NS * 32;    // q^_{i-1}: complex128 (psi) or complex64
-  static constexpr int STAGE = A_BYTES + B_BYTES;
-  static constexpr int QT = NS * 16;         // formed q^_i (complex64)
-  static constexpr int SMEM = STAGES * STAGE + 2 * QT;
+  static constexpr int A_BYTES = round128(NS * 16);   // y^_{i-1}: complex64 spinors
+  static constexpr int B_BYTES = round128(NS * 32);   // q^_{i-1}: complex128 (psi) or complex64
+  static constexpr int STAGE = A_BYTES + B_BYTES;     // tensor-copy destinations stay 128-byte aligned
+  static constexpr int QT = round128(NS * 16);        // formed q^_i (complex64)
+  static constexpr int SMEM = STAGES * STAGE + 2 * QT + 128;   // + alignment slack
 };
 
 // ---------------------------------------------------------------------------
@@ -89,6 +82,9 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)), "r"(bytes)
                : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ bool mbar_try(uint64_t* bar, unsigned parity) {
   unsigned ok;
@@ -130,49 +126,36 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
       : "memory");
 }
 
+// one box of a tensor map (2D: {x, y}; 3D: {x, y, z}) -> shared memory,
+// completion counted on `bar`; elements outside the tensor arrive as zeros
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar,
+                                            uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(saddr(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(saddr(bar)), "l"(pol)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar,
+                                            uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(saddr(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(saddr(bar)), "l"(pol)
+      : "memory");
+}
+
+// the tensor maps live in global memory, written by the host before the
+// launch: make them visible to the tensor copies of this kernel
+__device__ __forceinline__ void fence_tensormap(const CUtensorMap* map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
+}
+
 // generic-proxy writes to global memory (other CTAs' stores of the previous
 // pass) made visible to this thread's later bulk copies, and the reverse
 __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
 __device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(NC) : "memory"); }
-
-// ---------------------------------------------------------------------------
-// compensated FP32 arithmetic (value s plus error accumulator e)
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& r) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  r = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-// s + e  +=  (kh + kl) * (a - b)
-__device__ __forceinline__ void acc_diff(float kh, float kl, float a, float b, float& s, float& e) {
-  float d, de;
-  two_sum(a, -b, d, de);
-  const float p = __fmul_rn(kh, d);
-  const float pe = fmaf(kh, d, -p);
-  float t, r;
-  two_sum(s, p, t, r);
-  s = t;
-  e = __fadd_rn(e, __fadd_rn(pe, r));
-  e = fmaf(kh, de, e);
-  e = fmaf(kl, d, e);
-}
-// s + e  +=  (kh + kl) * a
-__device__ __forceinline__ void acc_prod(float kh, float kl, float a, float& s, float& e) {
-  const float p = __fmul_rn(kh, a);
-  const float pe = fmaf(kh, a, -p);
-  float t, r;
-  two_sum(s, p, t, r);
-  s = t;
-  e = __fadd_rn(e, __fadd_rn(pe, r));
-  e = fmaf(kl, a, e);
-}
-// s + e = (dh + dl) * a
-__device__ __forceinline__ void start_prod(float dh, float dl, float a, float& s, float& e) {
-  s = __fmul_rn(dh, a);
-  e = fmaf(dh, a, -s);
-  e = fmaf(dl, a, e);
-}
 
 // Coefficients of one pass of one problem, FP32 pairs.
 struct StencilCoef {
@@ -184,7 +167,10 @@ struct StencilCoef {
 };
 
 // (H - s - sigma) q^ - e q^_{i-1} at one site of the formed tile (row r,
-// column c of the rectangle), V given as a pair (vh, vl).
+// column c of the rectangle), V given as a pair (vh, vl).  FP32 products and
+// sums; every coefficient enters as a value plus its remainder, so that its
+// own rounding is not a constant perturbation of the operator (the diagonal
+// m c^2 - s - sigma reaches 2 m c^2).
 template <int R>
 __device__ __forceinline__ void site_stencil(const float4* qt, int r, int c, const StencilCoef& k, float vh, float vl,
                                              const float (&qp)[4], float4& C, float (&y)[4]) {
@@ -192,71 +178,38 @@ __device__ __forceinline__ void site_stencil(const float4* qt, int r, int c, con
   C = qt[r * W + c];
   const float4 E1 = qt[r * W + c + 1], W1 = qt[r * W + c - 1];
   const float4 N1 = qt[(r + 1) * W + c], S1 = qt[(r - 1) * W + c];
-  // diagonals with V: (a + v) as a pair
-  float duh, dul, ddh, ddl;
-  {
-    float r1, r2;
-    two_sum(k.auh, vh, duh, r1);
-    two_sum(k.adh, vh, ddh, r2);
-    dul = __fadd_rn(__fadd_rn(k.aul, vl), r1);
-    ddl = __fadd_rn(__fadd_rn(k.adl, vl), r2);
-  }
-  float s0, e0, s1, e1, s2, e2, s3, e3;
-  start_prod(duh, dul, C.x, s0, e0);
-  start_prod(duh, dul, C.y, s1, e1);
-  start_prod(ddh, ddl, C.z, s2, e2);
-  start_prod(ddh, ddl, C.w, s3, e3);
-  if constexpr (R == 1) {
-    // upper: c[-i D_x d - D_y d];  lower: c[-i D_x u + D_y u]
-    acc_diff(k.kxh, k.kxl, E1.w, W1.w, s0, e0);
-    acc_diff(-k.kyh, -k.kyl, N1.z, S1.z, s0, e0);
-    acc_diff(-k.kxh, -k.kxl, E1.z, W1.z, s1, e1);
-    acc_diff(-k.kyh, -k.kyl, N1.w, S1.w, s1, e1);
-    acc_diff(k.kxh, k.kxl, E1.y, W1.y, s2, e2);
-    acc_diff(k.kyh, k.kyl, N1.x, S1.x, s2, e2);
-    acc_diff(-k.kxh, -k.kxl, E1.x, W1.x, s3, e3);
-    acc_diff(k.kyh, k.kyl, N1.y, S1.y, s3, e3);
-  } else {
-    // D f = 8 (f[j+1] - f[j-1]) - (f[j+2] - f[j-2]), coefficient c / (12 h)
+  float dx[4] = {E1.x - W1.x, E1.y - W1.y, E1.z - W1.z, E1.w - W1.w};
+  float dy[4] = {N1.x - S1.x, N1.y - S1.y, N1.z - S1.z, N1.w - S1.w};
+  if constexpr (R == 2) {   // D f = 8 (f[j+1] - f[j-1]) - (f[j+2] - f[j-2]), coefficient c / (12 h)
     const float4 E2 = qt[r * W + c + 2], W2 = qt[r * W + c - 2];
     const float4 N2 = qt[(r + 2) * W + c], S2 = qt[(r - 2) * W + c];
-    const float x8h = 8.f * k.kxh, x8l = 8.f * k.kxl, y8h = 8.f * k.kyh, y8l = 8.f * k.kyl;
-    acc_diff(x8h, x8l, E1.w, W1.w, s0, e0);
-    acc_diff(-k.kxh, -k.kxl, E2.w, W2.w, s0, e0);
-    acc_diff(-y8h, -y8l, N1.z, S1.z, s0, e0);
-    acc_diff(k.kyh, k.kyl, N2.z, S2.z, s0, e0);
-    acc_diff(-x8h, -x8l, E1.z, W1.z, s1, e1);
-    acc_diff(k.kxh, k.kxl, E2.z, W2.z, s1, e1);
-    acc_diff(-y8h, -y8l, N1.w, S1.w, s1, e1);
-    acc_diff(k.kyh, k.kyl, N2.w, S2.w, s1, e1);
-    acc_diff(x8h, x8l, E1.y, W1.y, s2, e2);
-    acc_diff(-k.kxh, -k.kxl, E2.y, W2.y, s2, e2);
-    acc_diff(y8h, y8l, N1.x, S1.x, s2, e2);
-    acc_diff(-k.kyh, -k.kyl, N2.x, S2.x, s2, e2);
-    acc_diff(-x8h, -x8l, E1.x, W1.x, s3, e3);
-    acc_diff(k.kxh, k.kxl, E2.x, W2.x, s3, e3);
-    acc_diff(y8h, y8l, N1.y, S1.y, s3, e3);
-    acc_diff(-k.kyh, -k.kyl, N2.y, S2.y, s3, e3);
+    dx[0] = fmaf(8.f, dx[0], W2.x - E2.x); dx[1] = fmaf(8.f, dx[1], W2.y - E2.y);
+    dx[2] = fmaf(8.f, dx[2], W2.z - E2.z); dx[3] = fmaf(8.f, dx[3], W2.w - E2.w);
+    dy[0] = fmaf(8.f, dy[0], S2.x - N2.x); dy[1] = fmaf(8.f, dy[1], S2.y - N2.y);
+    dy[2] = fmaf(8.f, dy[2], S2.z - N2.z); dy[3] = fmaf(8.f, dy[3], S2.w - N2.w);
   }
-  // c (A_x sigma_x + A_y sigma_y) q
-  acc_prod(k.axh, k.axl, C.z, s0, e0);
-  acc_prod(k.axh, k.axl, C.w, s1, e1);
-  acc_prod(k.axh, k.axl, C.x, s2, e2);
-  acc_prod(k.axh, k.axl, C.y, s3, e3);
+  // diagonals with V as FP32 pairs: the sum (up to 2 m c^2) rounds differently
+  // at every site, so its rounding error goes into the remainder
+  float au, ad, ru, rd;
+  two_sum(k.auh, vh, au, ru);
+  two_sum(k.adh, vh, ad, rd);
+  const float aul = k.aul + vl + ru, adl = k.adl + vl + rd;
+  // upper: (mc^2+V-s-sigma) u + c[-i D_x d - D_y d + (A_x - i A_y) d]
+  // lower: (-mc^2+V-s-sigma) d + c[-i D_x u + D_y u + (A_x + i A_y) u]
+  float y0 = au * C.x + k.kxh * dx[3] - k.kyh * dy[2] + k.axh * C.z;
+  float y1 = au * C.y - k.kxh * dx[2] - k.kyh * dy[3] + k.axh * C.w;
+  float y2 = ad * C.z + k.kxh * dx[1] + k.kyh * dy[0] + k.axh * C.x;
+  float y3 = ad * C.w - k.kxh * dx[0] + k.kyh * dy[1] + k.axh * C.y;
   if (k.has_ay) {
-    acc_prod(k.ayh, k.ayl, C.w, s0, e0);
-    acc_prod(-k.ayh, -k.ayl, C.z, s1, e1);
-    acc_prod(-k.ayh, -k.ayl, C.y, s2, e2);
-    acc_prod(k.ayh, k.ayl, C.x, s3, e3);
+    y0 = fmaf(k.ayh, C.w, y0); y1 = fmaf(-k.ayh, C.z, y1);
+    y2 = fmaf(-k.ayh, C.y, y2); y3 = fmaf(k.ayh, C.x, y3);
   }
-  e0 = fmaf(-k.e, qp[0], e0);
-  e1 = fmaf(-k.e, qp[1], e1);
-  e2 = fmaf(-k.e, qp[2], e2);
-  e3 = fmaf(-k.e, qp[3], e3);
-  y[0] = __fadd_rn(s0, e0);
-  y[1] = __fadd_rn(s1, e1);
-  y[2] = __fadd_rn(s2, e2);
-  y[3] = __fadd_rn(s3, e3);
+  // remainders of the coefficients, and the coupling to q^_{i-1}
+  y0 = fmaf(aul, C.x, fmaf(k.kxl, dx[3], fmaf(-k.kyl, dy[2], fmaf(k.axl, C.z, fmaf(-k.e, qp[0], y0)))));
+  y1 = fmaf(aul, C.y, fmaf(-k.kxl, dx[2], fmaf(-k.kyl, dy[3], fmaf(k.axl, C.w, fmaf(-k.e, qp[1], y1)))));
+  y2 = fmaf(adl, C.z, fmaf(k.kxl, dx[1], fmaf(k.kyl, dy[0], fmaf(k.axl, C.x, fmaf(-k.e, qp[2], y2)))));
+  y3 = fmaf(adl, C.w, fmaf(-k.kxl, dx[0], fmaf(k.kyl, dy[1], fmaf(k.axl, C.y, fmaf(-k.e, qp[3], y3)))));
+  y[0] = y0; y[1] = y1; y[2] = y2; y[3] = y3;
 }
 
 // The input fields of pass i of problem pr: A = y^_{i-1} (complex64; none in
@@ -342,20 +295,36 @@ __device__ __forceinline__ unsigned row_copy(bool generic, const char* field, in
 }
 
 // Producer: the stage of one tile (all 32 threads of the producer warp).
+// By tensor copies, one box per field (zeros outside the grid; the
+// consumers patch periodic halos); else row by row.  Either way every byte
+// in flight is announced (expect-tx) before its copy is issued, and the
+// warp's single arrival comes last.
 template <int R>
-__device__ __forceinline__ void produce_tile(const Problem* pr, int i, int tt, unsigned char* stage, uint64_t* full,
-                                             bool diri, uint64_t pol) {
+__device__ __forceinline__ void produce_tile(const LaunchParams& lp, int b, const Problem* pr, int i, int tt,
+                                             unsigned char* stage, uint64_t* full, bool diri, uint64_t pol) {
   using G = Geo<R>;
   const int lane = threadIdx.x & 31;
   const int lt = tt - pr->tile_begin;
   const int x0 = (lt % pr->tiles_x) * TILE_W;
   const int y0 = (lt / pr->tiles_x) * TH;
-  const PassFields f = pass_fields(pr, i);
-  const int nf = (i == 1) ? 1 : 2;     // pass 1 reads psi only
   char* A = reinterpret_cast<char*>(stage);
   char* B = reinterpret_cast<char*>(stage) + G::A_BYTES;
+  if (pr->tma) {
+    if (lane == 0) {
+      const TmaMaps* mp = lp.maps + b;
+      const int xe = 4 * (x0 - R), ye = y0 - R;   // element coordinates (16- or 32-byte multiples)
+      const unsigned bytes = (i >= 2 ? G::NS * 16u : 0u) + (i <= 2 ? G::NS * 32u : G::NS * 16u);
+      mbar_arrive_expect_tx(full, bytes);
+      if (i >= 2) tma_load_3d(A, &mp->ybuf, xe, ye, (i - 1) & 1, full, pol);
+      if (i <= 2) tma_load_2d(B, &mp->psi, xe, ye, full, pol);
+      else tma_load_3d(B, &mp->basis, xe, ye, i - 3, full, pol);
+    }
+    return;
+  }
+  const PassFields f = pass_fields(pr, i);
+  const int nf = (i == 1) ? 1 : 2;     // pass 1 reads psi only
   unsigned bytes = 0;
-  // generic writes, then the arrival that announces the bulk bytes, then the copies
+  // generic writes first (zeros, narrow grids)
   for (int p = lane; p < nf * G::HR; p += 32) {
     const bool fb = (nf == 1) || p >= G::HR;
     const int r = fb && nf == 2 ? p - G::HR : p;
@@ -376,7 +345,7 @@ __device__ __forceinline__ void produce_tile(const Problem* pr, int i, int tt, u
     bytes += (unsigned)((cr - cl) * sb);
     if (!diri) bytes += (unsigned)((cl + (G::W - cr)) * sb);
   }
-  mbar_arrive_expect_tx(full, bytes);
+  if (bytes) mbar_expect_tx(full, bytes);
   for (int p = lane; p < nf * G::HR; p += 32) {
     const bool fb = (nf == 1) || p >= G::HR;
     const int r = fb && nf == 2 ? p - G::HR : p;
@@ -384,46 +353,8 @@ __device__ __forceinline__ void produce_tile(const Problem* pr, int i, int tt, u
     row_copy<R>(false, fb ? f.B : f.A, sb, (fb ? B : A) + r * G::W * sb, pr->nx, pr->ny, x0, y0 - R + r, diri, full,
                 pol);
   }
-}
-
-// psi <- C_1 psi + sum_{j >= 2} C_j q^_j at site s: the complex64 basis
-// terms accumulated in compensated FP32 (coefficients as FP32 pairs, exact
-// products, two-sum accumulation), added to the FP64 term C_1 psi at the end.
-// Loads of eight basis vectors are issued before their products.
-__device__ __forceinline__ void recombine_site_df(vec4* psi, const float4* basis, size_t n, size_t s, int k,
-                                                  const double* cr, const double* ci, const float* crh,
-                                                  const float* crl, const float* cih, const float* cil) {
-  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, e0 = 0.f, e1 = 0.f, e2 = 0.f, e3 = 0.f;
-  for (int j0 = 2; j0 <= k; j0 += 8) {
-    float4 v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u)
-      if (j0 + u <= k) v[u] = __ldcs(basis + (size_t)(j0 + u - 2) * n + s);
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      if (j0 + u <= k) {
-        const int j = j0 + u;
-        const float ah = crh[j], al = crl[j], bh = cih[j], bl = cil[j];
-        // (a + i b)(q.re + i q.im) for the upper (x, y) and lower (z, w) component
-        acc_prod(ah, al, v[u].x, s0, e0);
-        acc_prod(-bh, -bl, v[u].y, s0, e0);
-        acc_prod(ah, al, v[u].y, s1, e1);
-        acc_prod(bh, bl, v[u].x, s1, e1);
-        acc_prod(ah, al, v[u].z, s2, e2);
-        acc_prod(-bh, -bl, v[u].w, s2, e2);
-        acc_prod(ah, al, v[u].w, s3, e3);
-        acc_prod(bh, bl, v[u].z, s3, e3);
-      }
-    }
-  }
-  const vec4 q = psi[s];
-  const double ar = cr[1], ai = ci[1];
-  vec4 o;
-  o.x = fma(ar, q.x, fma(-ai, q.y, (double)s0 + (double)e0));
-  o.y = fma(ar, q.y, fma(ai, q.x, (double)s1 + (double)e1));
-  o.z = fma(ar, q.z, fma(-ai, q.w, (double)s2 + (double)e2));
-  o.w = fma(ar, q.w, fma(ai, q.z, (double)s3 + (double)e3));
-  psi[s] = o;
+  __syncwarp();
+  if (lane == 0) mbar_arrive(full);
 }
 
 __device__ __forceinline__ int problem_of_tile(const LaunchParams& lp, int t) {
@@ -450,10 +381,11 @@ __device__ __forceinline__ void pass_state(const LaunchParams& lp, const DevStat
 }
 
 template <int R, bool SINGLE>
-__global__ void __launch_bounds__(NT, 1) lanczos_step_m32(const __grid_constant__ LaunchParams lp,
+__global__ void __launch_bounds__(NT, 2) lanczos_step_m32(const __grid_constant__ LaunchParams lp,
                                                          const __grid_constant__ CoopArgs ca) {
   using G = Geo<R>;
-  extern __shared__ __align__(128) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* const smem = smem_raw + ((128u - (saddr(smem_raw) & 127u)) & 127u);
   __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES];
   __shared__ DevState sst;              // one problem: this CTA's copy of its scalars
   __shared__ double red[NCW][3];
@@ -470,7 +402,7 @@ __global__ void __launch_bounds__(NT, 1) lanczos_step_m32(const __grid_constant_
   const bool diri = lp.diri != 0;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full_bar[s], 32);
+      mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
     abort_s = 0;
@@ -501,11 +433,16 @@ __global__ void __launch_bounds__(NT, 1) lanczos_step_m32(const __grid_constant_
         pass_state<SINGLE>(lp, &sst, b, stopped, i);
         const int seg_end = min(t_end, pr->tile_begin + pr->ntiles);
         if (!stopped) {
+          if (pr->tma && lane == 0) {
+            fence_tensormap(&lp.maps[b].basis);
+            fence_tensormap(&lp.maps[b].ybuf);
+            fence_tensormap(&lp.maps[b].psi);
+          }
           for (int tt = t; tt < seg_end; ++tt, ++it) {
             const int s = it % STAGES;
             const unsigned ph = (it / STAGES) & 1u;
             if (!mbar_wait(&empty_bar[s], ph ^ 1u, &abort_s)) { failed = true; break; }
-            produce_tile<R>(pr, i, tt, smem + (size_t)s * G::STAGE, &full_bar[s], diri, pol);
+            produce_tile<R>(lp, b, pr, i, tt, smem + (size_t)s * G::STAGE, &full_bar[s], diri, pol);
           }
         }
         t = seg_end;
@@ -546,7 +483,10 @@ __global__ void __launch_bounds__(NT, 1) lanczos_step_m32(const __grid_constant_
         float4* y_out = (i < lp.m) ? static_cast<float4*>((i & 1) ? pr->ybuf1 : pr->ybuf0) : nullptr;
         const float* Vh = static_cast<const float*>(pr->V);
         const float* Vl = static_cast<const float*>(pr->Vlo);
-        double accP = 0.0, accY = 0.0, accX = 0.0;
+        // per-thread sums over the segment's tiles: FP32 values with two-sum
+        // compensation (FP64 arithmetic per tile would cost more than the
+        // tile's stencil: the FP64 pipe issues 1/64 of the FP32 rate)
+        float sP = 0.f, sY = 0.f, sX = 0.f, cP = 0.f, cY = 0.f, cX = 0.f;
         for (int tt = t; tt < seg_end; ++tt, ++it) {
           const int s = it % STAGES;
           const unsigned ph = (it / STAGES) & 1u;
@@ -558,17 +498,34 @@ __global__ void __launch_bounds__(NT, 1) lanczos_step_m32(const __grid_constant_
           const unsigned char* B = stage + G::A_BYTES;
           float4* qt = reinterpret_cast<float4*>(smem + (size_t)STAGES * G::STAGE + (size_t)(it & 1u) * G::QT);
           if (!mbar_wait(&full_bar[s], ph, &abort_s)) failed = true;
-          // q^_i at rectangle element e (B holds q^_{i-1} at sbB bytes per site)
-          auto formed = [&](int e, float (&qp)[4]) -> float4 {
+          // a tile staged by tensor copies holds zeros outside the grid; on
+          // periodic grids those elements are read from their images instead
+          const bool wrapfix = pr->tma && !diri &&
+                               (x0 < R || x0 + TILE_W + R > nx || y0 < R || y0 + TH + R > ny);
+          // q^_i at rectangle element e = (r, c) (B holds q^_{i-1} at sbB bytes per site)
+          auto formed = [&](int e, int r, int c, float (&qp)[4]) -> float4 {
+            bool glob = false;
+            size_t gi = 0;
+            if (wrapfix) {
+              const int gx = x0 - R + c, gy = y0 - R + r;
+              if (gx < 0 || gx >= nx || gy < 0 || gy >= ny) {
+                int ix = gx % nx, iy = gy % ny;
+                if (ix < 0) ix += nx;
+                if (iy < 0) iy += ny;
+                glob = true;
+                gi = (size_t)iy * nx + ix;
+              }
+            }
             if (f.sbB == 32) {
-              const double4_32a v = reinterpret_cast<const double4_32a*>(B)[e];
+              const double4_32a v = glob ? ldw4(reinterpret_cast<const vec4*>(f.B) + gi)
+                                         : reinterpret_cast<const double4_32a*>(B)[e];
               qp[0] = (float)v.x; qp[1] = (float)v.y; qp[2] = (float)v.z; qp[3] = (float)v.w;
             } else {
-              const float4 v = reinterpret_cast<const float4*>(B)[e];
+              const float4 v = glob ? reinterpret_cast<const float4*>(f.B)[gi] : reinterpret_cast<const float4*>(B)[e];
               qp[0] = v.x; qp[1] = v.y; qp[2] = v.z; qp[3] = v.w;
             }
             if (i == 1) return make_float4(qp[0], qp[1], qp[2], qp[3]);
-            const float4 yv = A[e];
+            const float4 yv = glob ? reinterpret_cast<const float4*>(f.A)[gi] : A[e];
             return make_float4(fmaf(-gdS, qp[0], gS * yv.x), fmaf(-gdS, qp[1], gS * yv.y),
                                fmaf(-gdS, qp[2], gS * yv.z), fmaf(-gdS, qp[3], gS * yv.w));
           };
@@ -576,22 +533,26 @@ __global__ void __launch_bounds__(NT, 1) lanczos_step_m32(const __grid_constant_
           if (!failed) {
 #pragma unroll
             for (int kk = 0; kk < RPT; ++kk) {
-              const int e = (tg + kk * NCW + R) * G::W + tx + R;
-              qt[e] = formed(e, qp[kk]);
+              const int r = tg + kk * NCW + R;
+              const int e = r * G::W + tx + R;
+              qt[e] = formed(e, r, tx + R, qp[kk]);
             }
             constexpr int NH_ROW = 2 * R * G::W, NH = NH_ROW + 2 * R * TH;
             for (int h = ctid; h < NH; h += NC) {
-              int e;
+              int r, c;
               if (h < NH_ROW) {         // the rows above and below (full width)
                 const int rr = h / G::W;
-                e = ((rr < R) ? rr : TH + rr) * G::W + h % G::W;
+                r = (rr < R) ? rr : TH + rr;
+                c = h % G::W;
               } else {                  // the columns left and right
                 const int h2 = h - NH_ROW;
                 const int cc = h2 % (2 * R);
-                e = (h2 / (2 * R) + R) * G::W + ((cc < R) ? cc : TILE_W + cc);
+                r = h2 / (2 * R) + R;
+                c = (cc < R) ? cc : TILE_W + cc;
               }
+              const int e = r * G::W + c;
               float dummy[4];
-              qt[e] = formed(e, dummy);
+              qt[e] = formed(e, r, c, dummy);
             }
           }
           consumer_sync();
@@ -616,15 +577,16 @@ __global__ void __launch_bounds__(NT, 1) lanczos_step_m32(const __grid_constant_
                 tX = fmaf(C.x, C.x, fmaf(C.y, C.y, fmaf(C.z, C.z, fmaf(C.w, C.w, tX))));
               }
             }
-            accP += (double)tP;
-            accY += (double)tY;
-            accX += (double)tX;
+            float t, r;
+            two_sum(sP, tP, t, r); sP = t; cP += r;
+            two_sum(sY, tY, t, r); sY = t; cY += r;
+            two_sum(sX, tX, t, r); sX = t; cX += r;
           }
         }
         // this CTA's share of problem b: warps -> CTA, one partial per slot
-        accP = warp_sum(accP);
-        accY = warp_sum(accY);
-        accX = warp_sum(accX);
+        double accP = warp_sum((double)sP + (double)cP);
+        double accY = warp_sum((double)sY + (double)cY);
+        double accX = warp_sum((double)sX + (double)cX);
         if (lane == 0) { red[warp][0] = accP; red[warp][1] = accY; red[warp][2] = accX; }
         consumer_sync();
         if (warp == 0) {
@@ -687,10 +649,18 @@ __global__ void __launch_bounds__(NT, 1) lanczos_step_m32(const __grid_constant_
     if (SINGLE) {
       if (warp == 0) {   // the grid totals, in the same order in every CTA
         double t0 = 0.0, t1 = 0.0, t2 = 0.0;
-        for (int c = lane; c < ca.G; c += 32) {
-          t0 += __ldcg(slots + 3 * c + 0);
-          t1 += __ldcg(slots + 3 * c + 1);
-          t2 += __ldcg(slots + 3 * c + 2);
+        for (int c0 = 0; c0 < ca.G; c0 += 5 * 32) {   // five slots per lane in flight at once
+          double v[5][3];
+#pragma unroll
+          for (int u = 0; u < 5; ++u) {
+            const int c = c0 + lane + 32 * u;
+            const double* ps = slots + 3 * (c < ca.G ? c : 0);
+            v[u][0] = c < ca.G ? __ldcg(ps + 0) : 0.0;
+            v[u][1] = c < ca.G ? __ldcg(ps + 1) : 0.0;
+            v[u][2] = c < ca.G ? __ldcg(ps + 2) : 0.0;
+          }
+#pragma unroll
+          for (int u = 0; u < 5; ++u) { t0 += v[u][0]; t1 += v[u][1]; t2 += v[u][2]; }
         }
         t0 = warp_sum(t0);
         t1 = warp_sum(t1);
@@ -781,8 +751,10 @@ cudaError_t launch_t(LaunchParams p, int n_sm, CoopArgs ca, cudaStream_t s) {
   cudaError_t e = occupancy_on_device(occ_dev, lanczos_step_m32<R, SINGLE>, NT, smem, &occ);
   if (e != cudaSuccess) return e;
   if (occ < 1) return cudaErrorCooperativeLaunchTooLarge;
-  // one CTA per SM (at most one per tile), each with at least one tile
-  int grid = std::max(1, std::min(p.total_tiles, n_sm));
+  // as many CTAs as are resident (two per SM for the order-2 stencil, whose
+  // rings fit twice in shared memory), at most one per tile, so that every
+  // CTA has a tile in every pass
+  int grid = std::max(1, std::min(p.total_tiles, n_sm * occ));
   if (SINGLE) grid = std::min(grid, ca.cap);
   p.chunk_q = p.total_tiles / grid;
   p.chunk_r = p.total_tiles % grid;

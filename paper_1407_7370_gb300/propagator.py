@@ -355,6 +355,11 @@ class BatchPropagator:
         nat.check(nat.lib().dirac_batch_set_fields(self._b, problem, ptr, float(A[0]), float(A[1]),
                                                    float(shift)))
 
+    def set_step_mode(self, mode: str = "auto"):
+        """'auto', 'passes' or 'one_launch' (see dirac_batch_set_step_mode)."""
+        code = {"auto": nat.STEP_AUTO, "passes": nat.STEP_PASSES, "one_launch": nat.STEP_ONE_LAUNCH}[mode]
+        nat.check(nat.lib().dirac_batch_set_step_mode(self._b, code))
+
     def set_launch_shape(self, tile_height: int, ctas_per_sm: int = 0):
         nat.check(nat.lib().dirac_batch_set_launch_shape(self._b, tile_height, ctas_per_sm))
 

@@ -136,6 +136,7 @@ def test_batch_kernel_launches_do_not_grow_with_problem_count():
     # the mixed path runs every pass of every problem and the recombination
     # as one launch per step
     bm = BatchPropagator(GRIDS, m_max=6, precision="mixed")
+    bm.set_step_mode("one_launch")
     for k in range(len(GRIDS)):
         bm.set_fields(k, shift=137.036 ** 2)
     psis = [torch.from_numpy(p[1].copy()).cuda() for p in probs]
@@ -323,16 +324,20 @@ def test_batch_sampled_problems_500_steps_at_target():
                          for s in range(steps)])
         A = np.zeros((steps, len(pick), 2))
         A[:, :, 0] = base[:, None] * a0s[pick][None, :]
-        bp = BatchPropagator([(g.nx, g.ny, g.dx, g.dy)] * len(pick), m_max=m, precision="mixed")
-        for j in range(len(pick)):
-            bp.set_fields(j, shift=C2)
-        psis = [torch.from_numpy(p.copy()).cuda() for p in psi0]
-        bp.steps(psis, steps, dt, m, A=A, info=True)
-        target = 1e-5 * steps * dt
-        errs = []
-        for j, f in enumerate(futs):
-            ref, _ = f.result()
-            errs.append(lz.rel_l2(psis[j].cpu().numpy(), ref))
-    print("mixed vs oracle after %d steps (p0, A0, rel L2):" % steps,
-          [(round(float(p0s[k]), 1), round(float(a0s[k]), 1), "%.2e" % e) for k, e in zip(pick, errs)])
-    assert max(errs) <= target, (errs, target)
+        outs = {}
+        for mode in ("passes", "one_launch"):   # both launch forms of the mixed path
+            bp = BatchPropagator([(g.nx, g.ny, g.dx, g.dy)] * len(pick), m_max=m, precision="mixed")
+            bp.set_step_mode(mode)
+            for j in range(len(pick)):
+                bp.set_fields(j, shift=C2)
+            psis = [torch.from_numpy(p.copy()).cuda() for p in psi0]
+            bp.steps(psis, steps, dt, m, A=A, info=True)
+            outs[mode] = [p.cpu().numpy() for p in psis]
+            bp.close()
+        refs = [f.result()[0] for f in futs]
+    target = 1e-5 * steps * dt
+    for mode, out in outs.items():
+        errs = [lz.rel_l2(a, r) for a, r in zip(out, refs)]
+        print("mixed (%s) vs oracle after %d steps (p0, A0, rel L2):" % (mode, steps),
+              [(round(float(p0s[k]), 1), round(float(a0s[k]), 1), "%.2e" % e) for k, e in zip(pick, errs)])
+        assert max(errs) <= target, (mode, errs, target)
