@@ -408,7 +408,7 @@ class BatchPropagator:
         ms = (ctypes.c_double * nat.KERNEL_KINDS)()
         n = (ctypes.c_longlong * nat.KERNEL_KINDS)()
         nat.check(nat.lib().dirac_batch_profile_read(self._b, ms, n))
-        return {"pass": (ms[0], n[0]), "recombine": (ms[1], n[1])}
+        return {"pass": (ms[0], n[0]), "recombine": (ms[1], n[1]), "step": (ms[2], n[2])}
 
     @property
     def kernel_launches(self) -> int:
