@@ -54,7 +54,9 @@ def STEP_BYTES_PER_SITE_MIXED(m):    # complex64 basis; psi read and written in 
 # DRAM traffic per launch from the last ncu capture of each kernel on the
 # configured grid, valid only for the kernel sources it was taken with (sha1
 # of dirac_kernels.cuh and dirac_step32.cu).
-TRAFFIC = {}
+TRAFFIC = {"lanczos_step<double>": ("dd85b08bb8f8", 1.639508e9 + 1.302828e9),
+           "lanczos_pass<float>": ("dd85b08bb8f8", 33.634816e6 + 0.698624e6),
+           "lanczos_step_m32": ("dd85b08bb8f8", 316.580352e6 + 487.045632e6)}
 
 
 def kernel_sha() -> str:

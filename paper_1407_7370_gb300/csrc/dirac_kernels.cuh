@@ -914,18 +914,20 @@ lanczos_pass(const __grid_constant__ LaunchParams lp) {
 // psi <- C_1 psi + sum_{j >= 2} C_j q^_j at site s: the complex64 basis
 // terms accumulated in compensated FP32 (coefficients as FP32 pairs, exact
 // products, two-sum accumulation), added to the FP64 term C_1 psi at the end.
-// Loads of sixteen basis vectors are issued before their products.
+// Loads of DEPTH basis vectors are issued before their products (more loads
+// in flight per thread, against more registers).
+template <int DEPTH>
 __device__ __forceinline__ void recombine_site_df(vec4* psi, const float4* basis, size_t n, size_t s, int k,
                                                   const double* cr, const double* ci, const float* crh,
                                                   const float* crl, const float* cih, const float* cil) {
   float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, e0 = 0.f, e1 = 0.f, e2 = 0.f, e3 = 0.f;
-  for (int j0 = 2; j0 <= k; j0 += 16) {
-    float4 v[16];
+  for (int j0 = 2; j0 <= k; j0 += DEPTH) {
+    float4 v[DEPTH];
 #pragma unroll
-    for (int u = 0; u < 16; ++u)
+    for (int u = 0; u < DEPTH; ++u)
       if (j0 + u <= k) v[u] = __ldcs(basis + (size_t)(j0 + u - 2) * n + s);
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
+    for (int u = 0; u < DEPTH; ++u) {
       if (j0 + u <= k) {
         const int j = j0 + u;
         const float ah = crh[j], al = crl[j], bh = cih[j], bl = cil[j];
@@ -1004,8 +1006,10 @@ __device__ __forceinline__ void recombine_site(vec4* psi, const void* basis_v, l
   }
 }
 
+// Three CTAs per SM (at most 85 registers), so that enough warps keep loads
+// in flight: the compensated sums make the mixed form arithmetic-heavy.
 template <bool MIXED>
-__global__ void __launch_bounds__(256) recombine(const __grid_constant__ RecombParams rp) {
+__global__ void __launch_bounds__(256, 3) recombine(const __grid_constant__ RecombParams rp) {
   asm volatile("griddepcontrol.wait;" ::: "memory");
   __shared__ double cr[KMAX + 2], ci[KMAX + 2];
   __shared__ float fr[KMAX + 2], fi[KMAX + 2], frl[KMAX + 2], fil[KMAX + 2];
@@ -1038,8 +1042,8 @@ __global__ void __launch_bounds__(256) recombine(const __grid_constant__ RecombP
   vec4* psi = const_cast<vec4*>(pr->psi);
   for (long long s = (long long)lb * blockDim.x + threadIdx.x; s < n; s += stride) {
     if constexpr (MIXED)
-      recombine_site_df(psi, static_cast<const float4*>(pr->basis), (size_t)n, (size_t)s, k, cr, ci, fr, frl, fi,
-                        fil);
+      recombine_site_df<8>(psi, static_cast<const float4*>(pr->basis), (size_t)n, (size_t)s, k, cr, ci, fr, frl,
+                           fi, fil);
     else
       recombine_site<false>(psi, pr->basis, n, s, k, cr, ci, fr, fi);
   }

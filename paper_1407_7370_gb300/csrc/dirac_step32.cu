@@ -714,7 +714,7 @@ __global__ void __launch_bounds__(NT, 2) lanczos_step_m32(const __grid_constant_
           for (int e = threadIdx.x; e < TILE_W * TH; e += NT) {
             const int x = x0 + (e & (TILE_W - 1)), y = y0 + e / TILE_W;
             if (x < pr->nx && y < pr->ny)
-              recombine_site_df(psi, static_cast<const float4*>(pr->basis), (size_t)n, (size_t)y * pr->nx + x, rk_s,
+              recombine_site_df<16>(psi, static_cast<const float4*>(pr->basis), (size_t)n, (size_t)y * pr->nx + x, rk_s,
                                 cr_s, ci_s, crh_s, crl_s, cih_s, cil_s);
           }
         }
