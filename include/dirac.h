@@ -284,9 +284,13 @@ dirac_status dirac_use_graphs(dirac_ctx* ctx, int enable);
  *     barrier every CTA sums all CTA partials in the same order and updates
  *     its own copy of the scalars.  Each barrier wait is bounded: a timeout
  *     ends the launch and the next read of the state reports DIRAC_ECUDA.
- *     On the mixed path the tiles are staged by tensor copies into a
- *     shared-memory ring by a producer warp, and batches run every problem
- *     in the same launch.
+ *     On the mixed path each pass is a register sweep, one warp per strip
+ *     of the grid, that recomputes y^_{i-1} from the basis instead of
+ *     storing it (a pass reads two basis vectors and writes one), and
+ *     batches run every problem in the same launch.
+ *   DIRAC_STEP_ONE_LAUNCH_TMA (mixed path only; FP64 as ONE_LAUNCH): one
+ *     cooperative launch per step whose tiles are staged by tensor copies
+ *     into a shared-memory ring by a producer warp.
  *   DIRAC_STEP_AUTO (default): one launch per step on the FP64 path (one
  *     CTA per SM), per-pass launches on the mixed path (eight CTAs per SM;
  *     measured faster there than the one-launch form).
@@ -295,6 +299,7 @@ dirac_status dirac_use_graphs(dirac_ctx* ctx, int enable);
 #define DIRAC_STEP_AUTO 0
 #define DIRAC_STEP_PASSES 1
 #define DIRAC_STEP_ONE_LAUNCH 2
+#define DIRAC_STEP_ONE_LAUNCH_TMA 3
 dirac_status dirac_set_step_mode(dirac_ctx* ctx, int mode);
 
 /*

@@ -87,6 +87,7 @@ __host__ __device__ inline PassCoef make_coef(double g, double gd, double e, dou
 
 struct DevState {
   PassCoef pc_cur;          // coefficients of the next pass to run
+  PassCoef pc_prev;         // those of the last accepted pass (its stencil shift and coupling)
   int cur_pass;             // the next pass to run (1-based; 0 reads as 1)
   int redo_left;            // re-runs of a pass still allowed in this step
   double alpha[KMAX + 2];   // T diagonal of H - s, index 1..k
@@ -425,6 +426,7 @@ __device__ inline void finish_pass(const LaunchParams& lp, const Problem* pr, De
       // bands, so alpha_{i+1} is close to alpha_{i-1}, not to alpha_i.
       const double sig = (i + 1 <= k_prev) ? alpha_next_prev : (i >= 2 ? alpha_im1 : alpha);
       st->sigma[i + 1] = sig;
+      st->pc_prev = pc_now;
       st->pc_cur = make_coef(rs, rs * dd, sq * rX, lp.mcc - shift - sig, -lp.mcc - shift - sig);
       st->cur_pass = i + 1;
     }

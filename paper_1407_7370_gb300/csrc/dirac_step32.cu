@@ -203,6 +203,8 @@ __device__ __forceinline__ void site_stencil(const float4* qt, int r, int c, con
   if (k.has_ay) {
     y0 = fmaf(k.ayh, C.w, y0); y1 = fmaf(-k.ayh, C.z, y1);
     y2 = fmaf(-k.ayh, C.y, y2); y3 = fmaf(k.ayh, C.x, y3);
+    y0 = fmaf(k.ayl, C.w, y0); y1 = fmaf(-k.ayl, C.z, y1);
+    y2 = fmaf(-k.ayl, C.y, y2); y3 = fmaf(k.ayl, C.x, y3);
   }
   // remainders of the coefficients, and the coupling to q^_{i-1}
   y0 = fmaf(aul, C.x, fmaf(k.kxl, dx[3], fmaf(-k.kyl, dy[2], fmaf(k.axl, C.z, fmaf(-k.e, qp[0], y0)))));

@@ -221,11 +221,20 @@ def test_eigs_48_grid_matches_dense_eigh():
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("z", [20.0, 60.0])
-def test_eigs_full_size_coulomb_2048(z):
+@pytest.mark.parametrize("z,min_found", [(1.0, 0), (20.0, 1), (60.0, 2)])
+def test_eigs_full_size_coulomb_2048(z, min_found):
     """2048x2048, dx = 0.02, V = -Z/sqrt(r^2 + 0.25), up to 400 iterations: the
     converged Ritz pairs satisfy the Eq. 10 residual identity with the GPU
-    Hamiltonian, lie in the window, and are orthonormal."""
+    Hamiltonian, lie in the window, and are orthonormal.
+
+    How many converge in 400 iterations depends on Z.  With central
+    differences the kinetic term tops out at c sqrt(2)/dx ~ 9700, so the
+    positive band runs from m c^2 to about m c^2 + 2350, and the negative band
+    lies 2 m c^2 ~ 37600 below it: the bound states sit at the inner edge of a
+    spectrum about 42000 wide, and the Krylov space resolves the deepest of
+    them first.  Measured: Z = 1 (binding of order 1 hartree) converges none
+    in 400 iterations, Z = 20 one (about -29.8), Z = 60 two or three.
+    """
     n = 2048
     g = wl.Grid(n, n, 0.02, 0.02)
     V = wl.smoothed_coulomb(g, z, 0.5)
@@ -236,7 +245,11 @@ def test_eigs_full_size_coulomb_2048(z):
     start = start + 1e-3 * wl.random_spinor(g, 2) * np.exp(-(x * x + y * y))[..., None]
     res = p.eigs(dev(start), n_want=8, max_iter=400, tol=1e-8, window=(-C * C, 0.0),
                  vectors=True)
-    assert res.values.size >= 1
+    assert res.iterations <= 400
+    assert res.values.size >= min_found
+    assert res.n_converged >= res.values.size
+    if res.values.size == 0:
+        return
     Y = res.vectors.reshape(res.values.size, -1)
     gram = (Y.conj() @ Y.T).cpu().numpy()
     assert np.max(np.abs(gram - np.eye(res.values.size))) <= 1e-8
