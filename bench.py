@@ -53,16 +53,16 @@ def STEP_BYTES_PER_SITE_MIXED(m):    # complex64 basis; psi read and written in 
 
 # DRAM traffic per launch from the last ncu capture of each kernel on the
 # configured grid, valid only for the kernel sources it was taken with (sha1
-# of dirac_kernels.cuh, dirac_step32.cu and dirac_sweep.cu).
-TRAFFIC = {"lanczos_step<double>": ("dd85b08bb8f8", 1.639508e9 + 1.302828e9),
-           "lanczos_pass<float>": ("dd85b08bb8f8", 33.634816e6 + 0.698624e6),
-           "lanczos_step_m32": ("dd85b08bb8f8", 316.580352e6 + 487.045632e6)}
+# of dirac_kernels.cuh and dirac_step32.cu).
+TRAFFIC = {"lanczos_step<double>": ("8c1f0ed96894", 1.637978e9 + 1.302432e9),
+           "lanczos_pass<float>": ("8c1f0ed96894", 33.643520e6 + 0.615680e6),
+           "lanczos_step_m32": ("8c1f0ed96894", 316.942336e6 + 487.331840e6)}
 
 
 def kernel_sha() -> str:
     import hashlib
     h = hashlib.sha1()
-    for name in ("dirac_kernels.cuh", "dirac_step32.cu", "dirac_sweep.cu"):
+    for name in ("dirac_kernels.cuh", "dirac_step32.cu"):
         h.update(open(os.path.join(ROOT, "paper_1407_7370_gb300", "csrc", name), "rb").read())
     return h.hexdigest()[:12]
 
@@ -131,8 +131,7 @@ def parse():
                     help="grid side of the laser-packet workload (profiling; default: the configured 1024)")
     ap.add_argument("--batch-compare-steps", type=int, default=None,
                     help="steps of the batched mixed-vs-FP64 comparison (profiling; default: the configured 2000)")
-    ap.add_argument("--only", choices=["fp64", "mixed", "mixed_one_launch", "mixed_one_launch_tma", "eigen", "adjoint",
-                                       "batch", "paper"],
+    ap.add_argument("--only", choices=["fp64", "mixed", "mixed_one_launch", "eigen", "adjoint", "batch", "paper"],
                     default=None,
                     help="run one path only (for profiling); prints a partial line")
     return ap.parse_args()
@@ -472,7 +471,7 @@ def measure_batch(args, torch, world, dist, gi, pk):
             b = STEP_BYTES_PER_SITE_MIXED(m) if prec == "mixed" else STEP_BYTES_PER_SITE(m)
             gbs = b * sites / (step_ms / 1e3 / step_n) / 1e9
             hbm_alg = {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                       "kernel": "lanczos_sweep" if prec == "mixed" else "lanczos_step<double>",
+                       "kernel": "lanczos_step_m32" if prec == "mixed" else "lanczos_step<double>",
                        "kernel_avg_us": 1e3 * step_ms / step_n, "bytes_per_site_per_step": b}
         else:
             sb = 16 if prec == "mixed" else 32
@@ -782,8 +781,8 @@ def _run_ours(args, crop_future):
             print(json.dumps({"partial": args.only, "result": r}), flush=True)
         return 0
     runs = {}
-    step_modes = {"mixed_one_launch": "one_launch", "mixed_one_launch_tma": "one_launch_tma"}
-    for key in ((args.only,) if args.only else ("fp64", "mixed", "mixed_one_launch", "mixed_one_launch_tma")):
+    step_modes = {"mixed_one_launch": "one_launch"}
+    for key in ((args.only,) if args.only else ("fp64", "mixed", "mixed_one_launch")):
         prec = "mixed" if key.startswith("mixed") else key
         prop = Propagator(g.nx, g.ny, g.dx, g.dy, m_max=m, precision=prec)
         prop.set_step_mode(step_modes.get(key, "auto"))
@@ -876,8 +875,7 @@ def _run_ours(args, crop_future):
                 "speedup_vs_fp64": f["t"] / x["t"]}
 
     mixed = mixed_obj(runs["mixed"], None)
-    mixed_one = mixed_obj(runs["mixed_one_launch"], "lanczos_sweep")
-    mixed_tma = mixed_obj(runs["mixed_one_launch_tma"], "lanczos_step_m32")
+    mixed_one = mixed_obj(runs["mixed_one_launch"], "lanczos_step_m32")
     line = None
     if rank == 0:
         line = {"metric": METRIC, "value": site_rate(f["t"], K), "unit": UNIT, "n_gpus": world,
@@ -907,7 +905,6 @@ def _run_ours(args, crop_future):
                                   "note": "other hardware and workload: context, not a target"},
                 "mixed": mixed,
                 "mixed_one_launch": mixed_one,
-                "mixed_one_launch_tma": mixed_tma,
                 "diagnostics": {"k_used": f["info"].k_used, "err_est_last": f["info"].err_est,
                                 "cum_err_est": f["info"].cum_err, "energy": f["info"].energy,
                                 "recombine_avg_us": None if fk["rec_s"] is None else fk["rec_s"] * 1e6}}

@@ -75,10 +75,13 @@ typedef struct {
  * boundaries, precision DIRAC_FP64 or DIRAC_MIXED, and Krylov dimension up
  * to m_max (1..DIRAC_KRYLOV_MAX).  DIRAC_FP64 computes everything in FP64.
  * DIRAC_MIXED keeps the state psi in complex128 but stores the Krylov basis
- * in complex64 and applies H in FP32, while the inner products are summed in
- * FP64 across warps and the scalars alpha, beta, the small exponential and
- * the recombination coefficients stay FP64; the recombination adds C_1 psi
- * in FP64.  Allocates the workspace: (m_max + 1) device fields of nx*ny
+ * in complex64 and applies H in FP32 (every coefficient as an FP32 value
+ * plus its remainder, the diagonal plus V by an exact two-sum), while the
+ * inner products are summed in FP64 across warps and the scalars alpha,
+ * beta, the small exponential and the recombination coefficients stay FP64;
+ * the recombination adds C_1 psi in FP64 and the other terms as compensated
+ * FP32 sums.  Energies are best given relative to m c^2 on this path
+ * (energy_shift of dirac_set_fields).  Allocates the workspace: (m_max + 1) device fields of nx*ny
  * sites (32 B per site for FP64, 16 B for MIXED).  cuda_stream is a cudaStream_t (NULL: the legacy default
  * stream).  On success *out owns the context.
  * Errors: DIRAC_EINVAL (nx, ny < 1; dx, dy, c <= 0; mass < 0; bad order,
@@ -284,13 +287,9 @@ dirac_status dirac_use_graphs(dirac_ctx* ctx, int enable);
  *     barrier every CTA sums all CTA partials in the same order and updates
  *     its own copy of the scalars.  Each barrier wait is bounded: a timeout
  *     ends the launch and the next read of the state reports DIRAC_ECUDA.
- *     On the mixed path each pass is a register sweep, one warp per strip
- *     of the grid, that recomputes y^_{i-1} from the basis instead of
- *     storing it (a pass reads two basis vectors and writes one), and
- *     batches run every problem in the same launch.
- *   DIRAC_STEP_ONE_LAUNCH_TMA (mixed path only; FP64 as ONE_LAUNCH): one
- *     cooperative launch per step whose tiles are staged by tensor copies
- *     into a shared-memory ring by a producer warp.
+ *     On the mixed path the tiles are staged by tensor copies into a
+ *     shared-memory ring by a producer warp, and batches run every problem
+ *     in the same launch.
  *   DIRAC_STEP_AUTO (default): one launch per step on the FP64 path (one
  *     CTA per SM), per-pass launches on the mixed path (eight CTAs per SM;
  *     measured faster there than the one-launch form).
@@ -299,7 +298,6 @@ dirac_status dirac_use_graphs(dirac_ctx* ctx, int enable);
 #define DIRAC_STEP_AUTO 0
 #define DIRAC_STEP_PASSES 1
 #define DIRAC_STEP_ONE_LAUNCH 2
-#define DIRAC_STEP_ONE_LAUNCH_TMA 3
 dirac_status dirac_set_step_mode(dirac_ctx* ctx, int mode);
 
 /*

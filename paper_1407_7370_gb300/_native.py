@@ -23,7 +23,7 @@ OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ESTATE = range(6)
 PERIODIC, DIRICHLET = 0, 1
 FP64, MIXED = 0, 1
 OBS_PX, OBS_PROJ = 0, 1
-STEP_AUTO, STEP_PASSES, STEP_ONE_LAUNCH, STEP_ONE_LAUNCH_TMA = 0, 1, 2, 3
+STEP_AUTO, STEP_PASSES, STEP_ONE_LAUNCH = 0, 1, 2
 PEAK_FP64, PEAK_FP32 = 0, 1
 
 

@@ -8,7 +8,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SOURCES = [os.path.join(HERE, "csrc", n) for n in ("dirac_capi.cu", "dirac_step.cu", "dirac_step32.cu",
-                                                    "dirac_sweep.cu", "dirac_eigs.cu", "dirac_adjoint.cu")]
+                                                    "dirac_eigs.cu", "dirac_adjoint.cu")]
 DEPS = SOURCES + [os.path.join(HERE, "csrc", "dirac_kernels.cuh"),
                   os.path.join(HERE, "csrc", "dirac_internal.h"),
                   os.path.join(ROOT, "include", "dirac.h")]

@@ -376,17 +376,13 @@ struct Engine {
   // FP64, one problem: one cooperative launch per step (lanczos_step)
   bool use_step_kernel(int np) const {
     if (np != 1 || !d_coop_slots || precision != DIRAC_FP64) return false;
-    return step_mode == DIRAC_STEP_AUTO || step_mode == DIRAC_STEP_ONE_LAUNCH ||
-           step_mode == DIRAC_STEP_ONE_LAUNCH_TMA;
+    return step_mode == DIRAC_STEP_AUTO || step_mode == DIRAC_STEP_ONE_LAUNCH;
   }
   // mixed precision, any number of problems: one cooperative launch per step
   // (lanczos_step_m32) when asked for; per-pass launches are the default
   // (measured faster: 1024^2 0.60 vs 0.65 ms per step, the 256-packet batch
   // 10.8 vs 12.3 ms)
-  bool use_m32() const { return precision == DIRAC_MIXED && step_mode == DIRAC_STEP_ONE_LAUNCH_TMA; }
-  // mixed precision, any number of problems: one cooperative launch per step
-  // whose passes are register sweeps (lanczos_sweep)
-  bool use_sweep() const { return precision == DIRAC_MIXED && step_mode == DIRAC_STEP_ONE_LAUNCH; }
+  bool use_m32() const { return precision == DIRAC_MIXED && step_mode == DIRAC_STEP_ONE_LAUNCH; }
   cudaError_t mark(int kind);
   dirac_status init(int n, const int* nx, const int* ny, const double* dx, const double* dy, double mass_,
                     double c_, int order_, int boundary_, int precision_, int m_max_, void* stream_);
@@ -468,8 +464,7 @@ dirac_status Engine::init(int n, const int* nx, const int* ny, const double* dx,
     q.n = (long long)q.nx * q.ny;
     q.tiles_x = (q.nx + TILE_W - 1) / TILE_W;
     q.slot_off = slots;
-    // at least one tile (or sweep unit) per slot, for every tiling a run may use
-    slots += (size_t)std::max(tiles_of(q.nx, q.ny, 16), sweep_units(q.nx, q.ny, 4));
+    slots += (size_t)tiles_of(q.nx, q.ny, 16);   // at least one tile per slot
     sites += q.n;
   }
   // workspace: (m_max - 1) basis fields + 2 y^ fields per problem, one block
@@ -617,16 +612,12 @@ dirac_status Engine::run(vec4* const* psi, int nsteps, double dt, int m, double 
     for (long long k = 0; k < 2LL * nsteps * np; ++k)
       if (!std::isfinite(a_xy[k])) return fail(DIRAC_EINVAL, "non-finite vector potential in the schedule");
   const bool m32 = use_m32();
-  const bool swp = use_sweep();
   const int th = m32 ? M32_TILE_H
-                     : (swp ? SWEEP_H
-                            : (shape.th ? shape.th
-                                        : (precision == DIRAC_FP64 ? fp64_tile_height(P, shape.n_sm) : 16)));
-  const int tw = swp ? sweep_width(order) : TILE_W;
-  // tile list for this tile shape
+                     : (shape.th ? shape.th : (precision == DIRAC_FP64 ? fp64_tile_height(P, shape.n_sm) : 16));
+  // tile list for this tile height
   int tt = 0;
   for (HostProblem& q : P) {
-    q.ntiles = ((q.nx + tw - 1) / tw) * ((q.ny + th - 1) / th);
+    q.ntiles = tiles_of(q.nx, q.ny, th);
     q.tile_begin = tt;
     tt += q.ntiles;
   }
@@ -676,7 +667,7 @@ dirac_status Engine::run(vec4* const* psi, int nsteps, double dt, int m, double 
     if (s != DIRAC_OK) return s;
     Problem& d = hp[b];
     std::memset(&d, 0, sizeof(d));
-    d.nx = q.nx; d.ny = q.ny; d.tiles_x = (q.nx + tw - 1) / tw; d.tile_begin = q.tile_begin; d.ntiles = q.ntiles;
+    d.nx = q.nx; d.ny = q.ny; d.tiles_x = q.tiles_x; d.tile_begin = q.tile_begin; d.ntiles = q.ntiles;
     d.rblk_begin = q.rblk_begin; d.rblk_count = q.rblk_count;
     d.psi = psi[b];
     d.basis = q.basis; d.ybuf0 = q.ybuf[0]; d.ybuf1 = q.ybuf[1];
@@ -755,18 +746,7 @@ dirac_status Engine::run(vec4* const* psi, int nsteps, double dt, int m, double 
     lp.pass = 1;
     lp.probe = 1;
     CUDA_TRY(mark(KIND_PASS));
-    if (swp) {   // the sweep's own tile list: its probe pass is a launch of the sweep kernel
-      CoopArgs cp;
-      cp.slots = d_coop_slots;
-      cp.bar = d_coop_bar;
-      cp.G = 0;
-      cp.cap = coop_cap;
-      cp.bar_count = 0;
-      CUDA_TRY(cudaMemsetAsync(d_coop_bar, 0, GRID_SYNC_WORDS * sizeof(unsigned), stream));
-      CUDA_TRY(launch_step_sweep(order, diri, lp, shape.n_sm, cp, stream));
-    } else {
-      CUDA_TRY(launch_pass(precision, order, diri, hasv, lp, ls, stream));
-    }
+    CUDA_TRY(launch_pass(precision, order, diri, hasv, lp, ls, stream));
     ++launches;
     lp.probe = 0;
     need_probe = false;
@@ -799,11 +779,10 @@ dirac_status Engine::run(vec4* const* psi, int nsteps, double dt, int m, double 
   ca32.cap = coop_cap;
   ca32.bar_count = barrier_extra;
   auto enqueue_step = [&](cudaStream_t st, bool count) -> dirac_status {
-    if (m32 || swp) {   // the whole step in one launch (the barrier words restart at zero)
+    if (m32) {   // the whole step in one launch (the barrier words restart at zero)
       CUDA_TRY(cudaMemsetAsync(d_coop_bar, 0, GRID_SYNC_WORDS * sizeof(unsigned), st));
       if (count) CUDA_TRY(mark(KIND_STEP));
-      if (swp) CUDA_TRY(launch_step_sweep(order, diri, lp, shape.n_sm, ca32, st));
-      else CUDA_TRY(launch_step_m32(order, diri, lp, shape.n_sm, ca32, st));
+      CUDA_TRY(launch_step_m32(order, diri, lp, shape.n_sm, ca32, st));
       if (count) {
         ++launches;
         CUDA_TRY(mark(KIND_END));
@@ -833,7 +812,7 @@ dirac_status Engine::run(vec4* const* psi, int nsteps, double dt, int m, double 
     std::memcpy(kp, &lk, sizeof(lk)); kp += sizeof(lk);
     std::memcpy(kp, &rp, sizeof(rp)); kp += sizeof(rp);
     std::memcpy(kp, &ls, sizeof(ls)); kp += sizeof(ls);
-    const int extra[3] = {precision + 2 * (int)m32 + 4 * (int)swp, (int)hasv, rgrid};
+    const int extra[3] = {precision + 2 * (int)m32, (int)hasv, rgrid};
     std::memcpy(kp, extra, sizeof(extra));
     if (!step_graph || key != graph_key) {
       if (!cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
@@ -848,7 +827,7 @@ dirac_status Engine::run(vec4* const* psi, int nsteps, double dt, int m, double 
       cudaGraphDestroy(g);
       if (e != cudaSuccess) { step_graph = nullptr; return fail(DIRAC_ECUDA, "graph instantiate: %s", cudaGetErrorString(e)); }
       graph_key = key;
-      graph_kernels = (m32 || swp) ? 1 : m + lp.redo_budget + 1;
+      graph_kernels = m32 ? 1 : m + lp.redo_budget + 1;
     }
     for (int s = 0; s < nsteps; ++s) {
       CUDA_TRY(cudaGraphLaunch(step_graph, stream));
@@ -1309,8 +1288,7 @@ dirac_status dirac_debug_barrier_timeout(dirac_ctx* ctx, void* psi_dev, double d
 
 dirac_status dirac_set_step_mode(dirac_ctx* ctx, int mode) {
   if (!ctx) return fail(DIRAC_EINVAL, "null context");
-  if (mode != DIRAC_STEP_AUTO && mode != DIRAC_STEP_PASSES && mode != DIRAC_STEP_ONE_LAUNCH &&
-      mode != DIRAC_STEP_ONE_LAUNCH_TMA)
+  if (mode != DIRAC_STEP_AUTO && mode != DIRAC_STEP_PASSES && mode != DIRAC_STEP_ONE_LAUNCH)
     return fail(DIRAC_EINVAL, "unknown step mode %d", mode);
   ctx->e.step_mode = mode;
   return DIRAC_OK;
@@ -1318,8 +1296,7 @@ dirac_status dirac_set_step_mode(dirac_ctx* ctx, int mode) {
 
 dirac_status dirac_batch_set_step_mode(dirac_batch* bt, int mode) {
   if (!bt) return fail(DIRAC_EINVAL, "null batch");
-  if (mode != DIRAC_STEP_AUTO && mode != DIRAC_STEP_PASSES && mode != DIRAC_STEP_ONE_LAUNCH &&
-      mode != DIRAC_STEP_ONE_LAUNCH_TMA)
+  if (mode != DIRAC_STEP_AUTO && mode != DIRAC_STEP_PASSES && mode != DIRAC_STEP_ONE_LAUNCH)
     return fail(DIRAC_EINVAL, "unknown step mode %d", mode);
   bt->e.step_mode = mode;
   return DIRAC_OK;

@@ -92,23 +92,6 @@ constexpr int M32_TILE_H = 16;
 cudaError_t launch_step_m32(int order, bool diri, const LaunchParams& p, int n_sm, const CoopArgs& ca,
                             cudaStream_t s);
 
-// Units of the mixed-precision sweep step (lanczos_sweep): strips of
-// sweep_width(order) columns by SWEEP_H rows, one warp each.  A warp's 32
-// lanes cover the strip and two stencil half widths on either side, since a
-// pass applies the stencil twice (it recomputes y^_{i-1}).
-constexpr int SWEEP_H = 16;
-constexpr int sweep_width(int order) { return 32 - 2 * order; }
-inline int sweep_units(int nx, int ny, int order) {
-  return ((nx + sweep_width(order) - 1) / sweep_width(order)) * ((ny + SWEEP_H - 1) / SWEEP_H);
-}
-
-// One mixed-precision time step of every problem in `p` as one cooperative
-// launch (lanczos_sweep); with p.probe set, only the probe pass (the
-// Rayleigh quotient of psi, the first stencil shift).  The tile list must
-// hold sweep units; ca as for launch_step_m32.
-cudaError_t launch_step_sweep(int order, bool diri, const LaunchParams& p, int n_sm, const CoopArgs& ca,
-                              cudaStream_t s);
-
 // One time step of the single problem in `p` as one cooperative launch
 // (lanczos_step); sets the grid, the chunks and ca.G.  ca.bar_count on entry:
 // arrivals the barriers wait for beyond the launch's CTAs (0; 1 only in the

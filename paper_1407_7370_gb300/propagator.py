@@ -250,9 +250,8 @@ class Propagator:
         nat.check(nat.lib().dirac_import_state(self._ctx, buf, len(state)))
 
     def set_step_mode(self, mode: str = "auto"):
-        """'auto', 'passes', 'one_launch' or 'one_launch_tma' (see dirac_set_step_mode)."""
-        code = {"auto": nat.STEP_AUTO, "passes": nat.STEP_PASSES, "one_launch": nat.STEP_ONE_LAUNCH,
-                "one_launch_tma": nat.STEP_ONE_LAUNCH_TMA}[mode]
+        """'auto', 'passes' or 'one_launch' (see dirac_set_step_mode)."""
+        code = {"auto": nat.STEP_AUTO, "passes": nat.STEP_PASSES, "one_launch": nat.STEP_ONE_LAUNCH}[mode]
         nat.check(nat.lib().dirac_set_step_mode(self._ctx, code))
 
     def profile(self, enable: bool = True):
@@ -357,9 +356,8 @@ class BatchPropagator:
                                                    float(shift)))
 
     def set_step_mode(self, mode: str = "auto"):
-        """'auto', 'passes', 'one_launch' or 'one_launch_tma' (see dirac_batch_set_step_mode)."""
-        code = {"auto": nat.STEP_AUTO, "passes": nat.STEP_PASSES, "one_launch": nat.STEP_ONE_LAUNCH,
-                "one_launch_tma": nat.STEP_ONE_LAUNCH_TMA}[mode]
+        """'auto', 'passes' or 'one_launch' (see dirac_batch_set_step_mode)."""
+        code = {"auto": nat.STEP_AUTO, "passes": nat.STEP_PASSES, "one_launch": nat.STEP_ONE_LAUNCH}[mode]
         nat.check(nat.lib().dirac_batch_set_step_mode(self._b, code))
 
     def set_launch_shape(self, tile_height: int, ctas_per_sm: int = 0):

@@ -84,7 +84,7 @@ def _problem(k, g):
                                                                ("mixed", 2, "periodic", 16, "one_launch"),
                                                                ("mixed", 4, "dirichlet", 16, "one_launch"),
                                                                ("mixed", 2, "dirichlet", 16, "one_launch"),
-                                                               ("mixed", 4, "periodic", 16, "one_launch_tma")])
+                                                               ("mixed", 4, "periodic", 16, "one_launch")])
 def test_batch_matches_oracle_per_problem(precision, order, boundary, th, mode):
     from paper_1407_7370_gb300 import BatchPropagator
     dt, m, steps = 1e-4, 8, 4
@@ -147,13 +147,6 @@ def test_batch_kernel_launches_do_not_grow_with_problem_count():
     psis = [torch.from_numpy(p[1].copy()).cuda() for p in probs]
     bm.steps(psis, 3, 1e-4, 6, info=True)
     assert bm.kernel_launches == 1 + 3 * 1
-    bt = BatchPropagator(GRIDS, m_max=6, precision="mixed")
-    bt.set_step_mode("one_launch_tma")
-    for k in range(len(GRIDS)):
-        bt.set_fields(k, shift=137.036 ** 2)
-    psis = [torch.from_numpy(p[1].copy()).cuda() for p in probs]
-    bt.steps(psis, 3, 1e-4, 6, info=True)
-    assert bt.kernel_launches == 1 + 3 * 1
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -337,7 +330,7 @@ def test_batch_sampled_problems_500_steps_at_target():
         A = np.zeros((steps, len(pick), 2))
         A[:, :, 0] = base[:, None] * a0s[pick][None, :]
         outs = {}
-        for mode in ("passes", "one_launch", "one_launch_tma"):   # every launch form of the mixed path
+        for mode in ("passes", "one_launch"):   # both launch forms of the mixed path
             bp = BatchPropagator([(g.nx, g.ny, g.dx, g.dy)] * len(pick), m_max=m, precision="mixed")
             bp.set_step_mode(mode)
             for j in range(len(pick)):

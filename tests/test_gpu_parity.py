@@ -182,17 +182,16 @@ def test_bitwise_deterministic(precision):
 @pytest.mark.parametrize("nx,ny", [(64, 64), (70, 64), (64, 44), (70, 44), (33, 17), (130, 47), (56, 16),
                                    (57, 17)])
 @pytest.mark.parametrize("boundary", ["periodic", "dirichlet"])
-@pytest.mark.parametrize("mode", ["one_launch", "one_launch_tma"])
-def test_mixed_one_launch_tile_shapes(nx, ny, boundary, mode):
-    """Both mixed one-launch steps on grids whose tiles (32 x 16) or sweep
-    strips (28 x 16) are whole, ragged in x, in y, or in both, against the
-    oracle: every tile, however its stage is filled (tensor copies with halo
-    patches, or row copies), and every strip gives the same product."""
+def test_mixed_one_launch_tile_shapes(nx, ny, boundary):
+    """The mixed one-launch step on grids whose tiles (32 x 16) are whole,
+    ragged in x, in y, or in both, against the oracle: every tile, however
+    its stage is filled (tensor copies with halo patches, or row copies),
+    gives the same product."""
     g = wl.Grid(nx, ny, 0.1, 0.1)
     psi0 = 0.1 * wl.random_spinor(g, nx + 7 * ny)
     b = ham.DIRICHLET if boundary == "dirichlet" else ham.PERIODIC
     out, _, _ = gpu_run(g, psi0, 1e-5, 8, 2, A=(1.0, 0.5), boundary=boundary, precision="mixed",
-                        step_mode=mode)
+                        step_mode="one_launch")
     ref, _ = lz.propagate(oracle_op(g, A=(1.0, 0.5), boundary=b), psi0.copy(), 1e-5, 8, 2)
     assert lz.rel_l2(out, ref) <= mixed_tol(2, 1e-5, hnorm(g, (1.0, 0.5)))
 
@@ -257,8 +256,7 @@ def test_host_buffer_call_equals_device_call():
     ("fp64", "auto", 1),
     ("mixed", "passes", 7 + 3 + 1),     # the mixed path keeps 2 + m / 5 spare launches
     ("mixed", "auto", 7 + 3 + 1),
-    ("mixed", "one_launch", 1),
-    ("mixed", "one_launch_tma", 1)])
+    ("mixed", "one_launch", 1)])
 def test_kernel_launch_count(precision, mode, per_step):
     g = wl.Grid(32, 32, 0.1, 0.1)
     _, _, prop = gpu_run(g, wl.positive_energy_packet(g), 1e-4, 7, 3, precision=precision,
@@ -267,8 +265,7 @@ def test_kernel_launch_count(precision, mode, per_step):
 
 
 @pytest.mark.parametrize("precision,mode", [("fp64", "one_launch"), ("fp64", "passes"),
-                                            ("mixed", "passes"), ("mixed", "one_launch"),
-                                            ("mixed", "one_launch_tma")])
+                                            ("mixed", "passes"), ("mixed", "one_launch")])
 @pytest.mark.parametrize("m", [1, 2, 3, 32])
 def test_krylov_dimension_extremes(precision, mode, m):
     """m = 1 (psi' = exp(-i alpha_1 dt) psi), m = 2 and the largest Krylov
@@ -446,7 +443,7 @@ def test_one_launch_step_agrees_with_per_pass_launches(precision, nx, ny, order,
     A = rng.uniform(-5, 5, size=(6, 2))
     shift = 137.036 ** 2 if precision == "mixed" else 0.0
     outs = {}
-    modes = ("passes", "one_launch") if precision == "fp64" else ("passes", "one_launch", "one_launch_tma")
+    modes = ("passes", "one_launch")
     for mode in modes:
         psi, inf, _ = gpu_run(g, psi0, 1e-4, 12, 6, V=V, order=order, boundary=boundary, tol=tol,
                               A_steps=A, precision=precision, step_mode=mode, shift=shift)
