@@ -59,6 +59,18 @@ TRAFFIC = {"lanczos_step<double>": ("8c1f0ed96894", 1.637978e9 + 1.302432e9),
            "lanczos_step_m32": ("8c1f0ed96894", 316.942336e6 + 487.331840e6)}
 
 
+def rounded(x, digits=6):
+    """x with every float rounded to `digits` significant digits (a shorter
+    JSON line; the measurements carry no more)."""
+    if isinstance(x, float):
+        return float("%.*g" % (digits, x)) if math.isfinite(x) else x
+    if isinstance(x, dict):
+        return {k: rounded(v, digits) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [rounded(v, digits) for v in x]
+    return x
+
+
 def kernel_sha() -> str:
     import hashlib
     h = hashlib.sha1()
@@ -349,7 +361,7 @@ def run_reference(args):
                              "sample": "%d time steps on a %dx%d crop of the workload"
                                        % (args.steps, side, side)},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    print(json.dumps(rounded(line)), flush=True)
     return 0
 
 
@@ -924,7 +936,7 @@ def _run_ours(args, crop_future):
             line["cpu_baseline"] = cpu_baseline()
         elif not args.no_cpu_baseline:
             line["cpu_baseline"] = None
-        print(json.dumps(line), flush=True)
+        print(json.dumps(rounded(line)), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
