@@ -380,8 +380,8 @@ struct Engine {
   }
   // mixed precision, any number of problems: one cooperative launch per step
   // (lanczos_step_m32) when asked for; per-pass launches are the default
-  // (measured faster: 1024^2 0.60 vs 0.65 ms per step, the 256-packet batch
-  // 10.8 vs 12.3 ms)
+  // (measured faster: 1024^2 0.51 vs 0.66 ms per step, 2048^2 1.58 vs 2.07
+  // ms, the 256-packet batch 9.2 vs 12.5 ms)
   bool use_m32() const { return precision == DIRAC_MIXED && step_mode == DIRAC_STEP_ONE_LAUNCH; }
   cudaError_t mark(int kind);
   dirac_status init(int n, const int* nx, const int* ny, const double* dx, const double* dy, double mass_,
