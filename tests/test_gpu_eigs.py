@@ -248,6 +248,9 @@ def test_eigs_full_size_coulomb_2048(z, min_found):
     assert res.iterations <= 400
     assert res.values.size >= min_found
     assert res.n_converged >= res.values.size
+    # the well binds: T_k has Ritz values below m c^2 even where none has
+    # converged yet (measured: 2 for Z = 1, 11 for Z = 20, 21 for Z = 60)
+    assert res.n_in_window >= 1
     if res.values.size == 0:
         return
     Y = res.vectors.reshape(res.values.size, -1)
