@@ -54,9 +54,9 @@ def STEP_BYTES_PER_SITE_MIXED(m):    # complex64 basis; psi read and written in 
 # DRAM traffic per launch from the last ncu capture of each kernel on the
 # configured grid, valid only for the kernel sources it was taken with (sha1
 # of dirac_kernels.cuh and dirac_step32.cu).
-TRAFFIC = {"lanczos_step<double>": ("8c1f0ed96894", 1.637978e9 + 1.302432e9),
-           "lanczos_pass<float>": ("8c1f0ed96894", 33.643520e6 + 0.615680e6),
-           "lanczos_step_m32": ("8c1f0ed96894", 316.942336e6 + 487.331840e6)}
+TRAFFIC = {"lanczos_step<double>": ("9b89fde1270a", 1.638854e9 + 1.302428e9),
+           "lanczos_pass<float>": ("9b89fde1270a", 33.635584e6 + 0.662016e6),
+           "lanczos_step_m32": ("9b89fde1270a", 316.990208e6 + 487.315200e6)}
 
 
 def rounded(x, digits=6):

@@ -865,24 +865,24 @@ __device__ __forceinline__ void pass_body(const LaunchParams& lp, const DevState
     if (!COOP && last_flag) {
       // the problem is complete: the whole CTA sums its slots in a fixed
       // order (thread-strided, the warp tree, then the warps in turn), the
-      // loads batched so that their L2 round trips overlap
+      // loads of SB slots per thread in flight at once, so that a pass of
+      // eight CTAs per SM waits for two L2 round trips here, not five
       const int cta_lo = cta_of_tile(pr->tile_begin, cq, cr);
       const int nslots = cta_of_tile(pr->tile_begin + pr->ntiles - 1, cq, cr) - cta_lo + 1;
+      constexpr int SB = 5;
       double t0 = 0.0, t1 = 0.0, t2 = 0.0;
-      int s = threadIdx.x;
-      for (; s + NT < nslots; s += 2 * NT) {
-        const double* p0 = pr->partials + 3 * s;
-        const double* p1 = p0 + 3 * NT;
-        const double a0 = __ldcg(p0), a1 = __ldcg(p0 + 1), a2 = __ldcg(p0 + 2);
-        const double c0 = __ldcg(p1), c1 = __ldcg(p1 + 1), c2 = __ldcg(p1 + 2);
-        t0 += a0 + c0;
-        t1 += a1 + c1;
-        t2 += a2 + c2;
-      }
-      for (; s < nslots; s += NT) {
-        t0 += __ldcg(pr->partials + 3 * s + 0);
-        t1 += __ldcg(pr->partials + 3 * s + 1);
-        t2 += __ldcg(pr->partials + 3 * s + 2);
+      for (int s0 = threadIdx.x; s0 < nslots; s0 += SB * NT) {
+        double v[SB][3];
+#pragma unroll
+        for (int k = 0; k < SB; ++k) {
+          const int s = s0 + k * NT;
+          const double* ps = pr->partials + 3 * (s < nslots ? s : 0);
+          v[k][0] = s < nslots ? __ldcg(ps + 0) : 0.0;
+          v[k][1] = s < nslots ? __ldcg(ps + 1) : 0.0;
+          v[k][2] = s < nslots ? __ldcg(ps + 2) : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < SB; ++k) { t0 += v[k][0]; t1 += v[k][1]; t2 += v[k][2]; }
       }
       t0 = warp_sum(t0);
       t1 = warp_sum(t1);
